@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""DAFMM matrix-vector product throughput on GB300 (Munknowns/s).
+
+One step = one application of the DAFMM operator A = I + kappa^2 diag(q) K~
+(upward pass, M2L, downward pass, near field, epilogue) to one synthetic
+right-hand side of the 128 x 128 grid, kappa = 40, 4-bump contrast
+(N = 16384), through the C-ABI call dafmm_matvec.  The headline value is the
+mixed-precision application (complex64 operators, FP32 arithmetic); the FP64
+application is timed in the same run and reported beside it.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the
+same workload, a bounded sample of rows per step, on the host cores.
+
+Multi-GPU runs (torchrun) run one independent replica per rank: a single
+problem has no data-parallel split, so value = all ranks'
+unknowns / max-over-ranks time and scaling is "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2204_00326_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DAFMM matvec Munknowns/s; time-to-1e-8 residual, mixed vs FP64 on GB300"
+FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=W.GRID128_K40.name, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--eps-nca", type=float, default=1e-12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            self.proc = subprocess.Popen([exe, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, target_s: float, seed: int = 21):
+    """The FP64 oracle's row-by-row matvec on a bounded sample of rows."""
+    import oracle
+
+    xy = oracle.grid_nodes(w.n_side)
+    q = W.contrast(w, xy)
+    v = W.random_vector(w.N, 1, seed=seed)[:, 0]
+    rng = np.random.default_rng(seed)
+    probe = np.sort(rng.choice(w.N, 16, replace=False))
+    t0 = time.perf_counter()
+    oracle.matvec_rows(w.n_side, w.kappa, q, v, probe)
+    tp = time.perf_counter() - t0
+    nrows = int(min(w.N, max(16, 16 * target_s / max(tp, 1e-6))))
+    rows = np.sort(rng.choice(w.N, nrows, replace=False))
+    t0 = time.perf_counter()
+    oracle.matvec_rows(w.n_side, w.kappa, q, v, rows)
+    dt = time.perf_counter() - t0
+    return {"value": nrows / dt / 1e6, "unit": "Munknowns/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{nrows} of {w.N} rows of A v (entries generated by quadrature, FP64), {dt:.1f} s"}
+
+
+def run_reference(a, w):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    xy = oracle.grid_nodes(w.n_side)
+    q = W.contrast(w, xy)
+    v = W.random_vector(w.N, 1, seed=21)[:, 0]
+    rng = np.random.default_rng(21)
+    probe = np.sort(rng.choice(w.N, 8, replace=False))
+    t0 = time.perf_counter()
+    oracle.matvec_rows(w.n_side, w.kappa, q, v, probe)
+    tp = (time.perf_counter() - t0) / 8
+    per_step = max(1.0, 150.0 / max(1, a.steps + a.warmup))  # whole run within a few minutes
+    nrows = int(min(w.N, max(8, per_step / max(tp, 1e-9))))
+    for _ in range(a.warmup):
+        oracle.matvec_rows(w.n_side, w.kappa, q, v, rng.choice(w.N, nrows, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.matvec_rows(w.n_side, w.kappa, q, v, rng.choice(w.N, nrows, replace=False))
+    dt = time.perf_counter() - t0
+    value = a.steps * nrows / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Munknowns/s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_side": w.n_side, "N": w.N, "kappa": w.kappa, "precision": "fp64 oracle",
+                       "rows_per_step": nrows},
+            "cpu_baseline": {"value": value, "unit": "Munknowns/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{nrows} of {w.N} rows of A v per step"},
+            "e2e": {"value": value, "unit": "Munknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    w = W.WORKLOADS[a.workload]
+    if a.impl == "reference":
+        run_reference(a, w)
+        return
+    rank, world, local = _dist_env()
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import paper_2204_00326_gb300 as pkg
+
+    pkg.build()
+    from paper_2204_00326_gb300 import native as N
+    from paper_2204_00326_gb300.operator import DafmmOperator
+
+    t0 = time.perf_counter()
+    op = DafmmOperator(w.n_side, w.kappa, lambda xy: W.contrast(w, xy), eps_nca=a.eps_nca)
+    setup_s = time.perf_counter() - t0
+    st = op.stats()
+    stream = torch.cuda.current_stream()
+    v = torch.as_tensor(W.random_vector(w.N, 1, seed=1 + rank)[:, 0], device="cuda")
+    out = torch.empty_like(v)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(prec, steps, profile):
+        for _ in range(a.warmup):
+            flush.zero_()
+            op.matvec(v, out, prec)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            N.dafmm_profile(op.ops, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()  # L2 flush between timed steps, outside the events
+            e0.record(stream)
+            op.matvec(v, out, prec)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        prof = None
+        if profile:
+            prof = N.dafmm_profile_read(op.ops)
+            N.dafmm_profile(op.ops, False)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return ms, prof
+
+    with ClockSampler(local) as clk:
+        ms_mixed, prof_mixed = timed(N.DAFMM_MIXED, a.steps, True)
+    ms_fp64, prof_fp64 = timed(N.DAFMM_FP64, a.steps, True)
+
+    # end to end: pinned host input -> device -> matvec -> pinned host output
+    vh = v.cpu().pin_memory()
+    oh = torch.empty_like(vh).pin_memory()
+    vd = torch.empty_like(v)
+    for _ in range(a.warmup):
+        vd.copy_(vh, non_blocking=True)
+        op.matvec(vd, out, N.DAFMM_MIXED)
+        oh.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        vd.copy_(vh, non_blocking=True)
+        op.matvec(vd, out, N.DAFMM_MIXED)
+        oh.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = t.item()
+
+    units = float(w.N) * world * a.steps
+    value = units / (ms_mixed * 1e-3) / 1e6
+    value64 = units / (ms_fp64 * 1e-3) / 1e6
+    e2e = units / (ms_e2e * 1e-3) / 1e6
+
+    hbm, peak_kind = _peaks()
+    # dominant kernel: the block-sparse transfer kernel (P2M, M2M, M2L, L2L launches)
+    bsr_cmacs = st.cmacs_up + st.cmacs_m2l + st.cmacs_down
+
+    def roof(prof, csize):
+        calls = max(1, prof.calls)
+        ms = (prof.ms_up + prof.ms_m2l + prof.ms_down) / calls
+        bytes_alg = bsr_cmacs * csize + st.coef_bytes_per_rhs * csize / 16.0 + w.N * csize
+        return ms, bytes_alg
+
+    ms_b, bytes_b = roof(prof_mixed, 8)
+    achieved = bytes_b / (ms_b * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "bsr_apply_kernel<float> (P2M, M2M, M2L, L2L)",
+                "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "ms_per_launch_group": ms_b, "algorithmic_bytes_per_step": bytes_b,
+                "pass_ms": {"up": prof_mixed.ms_up / max(1, prof_mixed.calls), "m2l": prof_mixed.ms_m2l / max(1, prof_mixed.calls),
+                            "down": prof_mixed.ms_down / max(1, prof_mixed.calls), "leaf": prof_mixed.ms_leaf / max(1, prof_mixed.calls)}}
+    ms_b64, _ = roof(prof_fp64, 16)
+    flops64 = 8.0 * bsr_cmacs
+    fp64_peak_gflops = 1250.0
+    roof64 = {"bound": "alu", "achieved": flops64 / (ms_b64 * 1e-3) / 1e9, "peak": fp64_peak_gflops, "unit": "GFLOP/s",
+              "frac": flops64 / (ms_b64 * 1e-3) / 1e9 / fp64_peak_gflops, "kernel": "bsr_apply_kernel<double>",
+              "peak_kind": "nominal GB300 FP64 rate"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(w, a.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Munknowns/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_mixed / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": w.name, "n_side": w.n_side, "N": w.N, "kappa": w.kappa, "contrast": w.contrast,
+                   "nbumps": w.nbumps, "nrhs": 1, "precision": "mixed (complex64 operators, FP32 math)",
+                   "eps_nca": a.eps_nca, "l2": "flushed: 256 MiB write between timed steps", "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": "Munknowns/s", "h2d_bytes_per_step": w.N * 16, "d2h_bytes_per_step": w.N * 16},
+        "gpu_launches": int(st.launches_per_call * a.steps),
+        "clocks": clk.summary(),
+        "fp64": {"value": value64, "unit": "Munknowns/s", "ms_per_step": ms_fp64 / a.steps, "dtype": "c128", "roofline": roof64,
+                 "gpu_launches": int(st.launches_per_call_fp64 * a.steps)},
+        "setup_s": {"total": setup_s, "entry_table": st.setup_seconds_table, "nca": st.setup_seconds_nca},
+        "operator": {"bytes_fp32": st.operator_bytes_fp32, "bytes_fp64": st.operator_bytes_fp64,
+                     "cmacs_per_rhs": st.cmacs_per_rhs},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    op.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

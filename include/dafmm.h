@@ -1,0 +1,214 @@
+/*
+ * dafmm.h -- C-ABI of the GB300 (sm_103a) library for the Directional
+ * Algebraic FMM (DAFMM) matrix-vector product of Gujjula & Ambikasaran,
+ * arXiv 2204.00326, applied to the discretised Lippmann-Schwinger equation.
+ *
+ * The operator.  On a uniform quadtree over [x0,x1]^2 with p x p first-kind
+ * Chebyshev nodes per leaf (Section 2, Eq. 7-9), the unknowns are psi at the
+ * N = n_side^2 nodes and the discrete system is A psi = f (Eq. 12a) with
+ *     A = I + kappa^2 diag(q) K,
+ *     K_ij = int_{B(j)} G(x_i, y) L_{j'}(y) dy,  G = (i/4) H0^(1)(kappa|x-y|),
+ * L_{j'} the least-squares cardinal function of leaf B(j) (Eq. 11, Eq. 13).
+ * dafmm_matvec applies the NCA-compressed K (Section 4-5) and the diagonal
+ * epilogue.
+ *
+ * Conventions for every call:
+ *   - Return value: DAFMM_OK (0) or one of the DAFMM_E* codes below; the text
+ *     of the last error on the calling thread is available from
+ *     dafmm_last_error().  No call aborts the process.
+ *   - Handles (dafmm_tree, dafmm_ops) are opaque, owned by the library and
+ *     released with tree_destroy / ops_destroy.  An ops handle keeps a
+ *     reference to its tree: destroy the ops before the tree.
+ *   - Arrays named *_dev are device pointers in the current CUDA device's
+ *     memory, owned by the caller; *_host are host pointers.  Complex vectors
+ *     are interleaved (re, im) doubles.  Vectors with several right-hand sides
+ *     are stored [N][nrhs] (right-hand side fastest).
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream enqueue their kernels on it and do
+ *     not synchronise the device unless stated.
+ *   - Unknowns are ordered leaf by leaf in Morton (Z) order of the leaves
+ *     (x bit below y bit); inside a leaf, node i' = k1 + p*k2 sits at
+ *     alpha + beta (zeta_k1, zeta_k2), zeta_k = -cos((2k+1) pi / (2p)).
+ *   - There is no CPU fallback: without a CUDA device every call that needs
+ *     one returns DAFMM_ECUDA.
+ */
+#ifndef DAFMM_H
+#define DAFMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define DAFMM_OK 0
+#define DAFMM_EBADARG 1     /* invalid argument or unsupported configuration */
+#define DAFMM_ENOMEM 2      /* host or device allocation failed */
+#define DAFMM_ENOTCONV 3    /* iterative solver stopped before the tolerance */
+#define DAFMM_EBREAKDOWN 4  /* numerical breakdown (singular pivot block, ...) */
+#define DAFMM_ETIMEOUT 5    /* a bounded device-side wait gave up */
+#define DAFMM_ECUDA 6       /* CUDA runtime error or no device */
+
+/* Arithmetic of an operator application. */
+#define DAFMM_FP64 0        /* complex128 operators and vectors, FP64 math */
+#define DAFMM_MIXED 1       /* complex64 operators and coefficients, FP32 math;
+                               boundary vectors stay complex128 */
+
+/* Parameters of the discretisation and of the compression (Section 3-4). */
+typedef struct dafmm_params {
+    int p;            /* Chebyshev nodes per leaf side; this build supports p = 4 */
+    double kappa;     /* wavenumber kappa > 0 (Eq. 1) */
+    double T;         /* a box of half-width w is high-frequency iff (kappa w)^2 > T
+                         (Section 3; the paper leaves T open, 16 is the default) */
+    double eps_nca;   /* tolerance of the partially pivoted ACA that picks the
+                         NCA pivots (Section 4.2.2, Rjasanow's stopping rule) */
+    int max_rank;     /* cap on every NCA rank; 0 = no cap */
+    int reserved[7];  /* must be zero */
+} dafmm_params;
+
+/* Shape of a built tree (filled by tree_info). */
+typedef struct dafmm_tree_info {
+    long N;           /* number of unknowns n_side^2 */
+    int n_side;       /* nodes per side */
+    int levels;       /* L + 1: levels 0 (root) .. L (leaves) */
+    int top;          /* coarsest level with a non-empty interaction list
+                         (levels > L when there is no far field) */
+    int hf[32];       /* per level: 1 if high-frequency (Section 3.2) */
+    int cones[32];    /* per level: number of cones (1 for low frequency) */
+    long il_pairs[32];/* per level: number of interaction-list pairs */
+} dafmm_tree_info;
+
+/* Realised sizes of a built operator (filled by dafmm_stats). */
+typedef struct dafmm_stats_t {
+    int rank_in_max[32];    /* per level: largest incoming rank */
+    int rank_out_max[32];   /* per level: largest outgoing rank */
+    double rank_in_mean[32];
+    double rank_out_mean[32];
+    long slots[32];         /* per level: active (box, cone) pairs */
+    double operator_bytes_fp64;   /* stored operators, complex128 */
+    double operator_bytes_fp32;   /* stored operators, complex64 */
+    double vector_bytes_per_rhs;  /* algorithmic vector/coefficient traffic of
+                                     one application, complex128, per RHS */
+    double cmacs_per_rhs;         /* complex multiply-adds of one application */
+    double setup_seconds_table;   /* entry-table kernel */
+    double setup_seconds_nca;     /* pivots and operators */
+    long p2p_cmacs_per_rhs;       /* part of cmacs_per_rhs spent in the near field */
+    double cmacs_up;              /* per RHS: P2M, M2M, directional M2M */
+    double cmacs_m2l;             /* per RHS: M2L, directional M2L */
+    double cmacs_down;            /* per RHS: directional L2L, L2L (not L2P) */
+    double cmacs_leaf;            /* per RHS: L2P + near field */
+    double coef_bytes_per_rhs;    /* multipole/local coefficients written and
+                                     read once each, complex128 */
+    int launches_per_call;        /* kernels one dafmm_matvec launches (mixed) */
+    int launches_per_call_fp64;   /* ... in FP64 */
+} dafmm_stats_t;
+
+/* Device time of the passes of the profiled dafmm_matvec calls (ms, summed). */
+typedef struct dafmm_profile_t {
+    long calls;
+    double ms_total;  /* first to last kernel of each call */
+    double ms_up;     /* P2M + M2M (+ the complex64 conversion in mixed mode) */
+    double ms_m2l;    /* M2L at every level */
+    double ms_down;   /* L2L into the leaves' locals */
+    double ms_leaf;   /* L2P + near field + epilogue */
+} dafmm_profile_t;
+
+typedef struct dafmm_tree dafmm_tree;
+typedef struct dafmm_ops dafmm_ops;
+
+/* Copy the message of the last failed call on this thread into buf (always
+ * NUL-terminated when size > 0).  Returns the status code of that call. */
+int dafmm_last_error(char* buf, size_t size);
+
+/*
+ * build_tree -- uniform quadtree on [x0,x1]^2 with n_side nodes per side
+ * (n_side = p * 2^L), its high/low-frequency regimes (Section 3), cones
+ * (Section 3.2.1, angle 2 pi / 2^ceil(log2(2 pi kappa w)) at the finest
+ * high-frequency level, doubling per level up), neighbour and interaction
+ * lists (Table 1).  Host work only; no device memory is used.
+ * Errors: DAFMM_EBADARG for p != 4, n_side not p times a power of two,
+ * x1 <= x0, kappa <= 0, eps_nca outside (0, 1), or leaves in the
+ * high-frequency regime.
+ */
+int build_tree(const dafmm_params* params, int n_side, double x0, double x1, dafmm_tree** out);
+
+/* Coordinates of the N unknowns (xy_host: N x 2 doubles, caller-owned). */
+int tree_nodes(const dafmm_tree* tree, double* xy_host);
+
+/* Shape of the tree (see dafmm_tree_info). */
+int tree_info(const dafmm_tree* tree, dafmm_tree_info* info);
+
+/*
+ * tree_check -- self-check of the lists (host only).  Counts, into *bad, the
+ * ordered leaf pairs that are not covered exactly once by the near field
+ * (same-level neighbours at the leaves) plus the interaction lists of their
+ * ancestors (Section 5: every interaction is either near or transferred at
+ * exactly one level), and the directional list entries whose mirror entry
+ * is missing (Table 1: B lies in the cone of A that points back at B).
+ * Cost O(nleaf^2 L): meant for small trees.
+ */
+int tree_check(const dafmm_tree* tree, long* bad);
+
+/* Release a tree.  NULL is accepted. */
+int tree_destroy(dafmm_tree* tree);
+
+/*
+ * build_nca_operators -- setup of the DAFMM operator for the contrast q.
+ *   1. On the device, tabulates K for every leaf offset of the uniform grid
+ *      (the near-field singular integrals and the far-field Gauss-Legendre
+ *      integrals of Section 2.3 are translation invariant per level).
+ *   2. Traverses the tree upwards and picks the nested pivots by partially
+ *      pivoted ACA (Section 4.2.2), forming the P2M/M2M, L2L/L2P (Section
+ *      4.2.1, all four cases) and M2L operators (Section 5 step 4).  K, not
+ *      A, is compressed; kappa^2 q enters in the epilogue (Eq. 13).
+ *   3. Uploads complex128 and complex64 copies of every operator.
+ * q_dev: N doubles on the device (copied; the caller may free it after the
+ * call returns).  The call synchronises the stream.
+ * Errors: DAFMM_EBADARG, DAFMM_ENOMEM, DAFMM_EBREAKDOWN (a singular pivot
+ * block), DAFMM_ECUDA.
+ */
+int build_nca_operators(dafmm_tree* tree, const double* q_dev, void* stream, dafmm_ops** out);
+
+/*
+ * dafmm_matvec -- out = A v = v + kappa^2 q .* (K~ v) for nrhs right-hand
+ * sides, K~ the DAFMM approximation of K: upward pass (P2M, M2M, directional
+ * M2M), transverse pass (M2L, directional M2L), downward pass (directional
+ * L2L, L2L, L2P) and near field (Section 5 steps 3-6).
+ * v_dev, out_dev: N x nrhs complex128 (interleaved) on the device; they must
+ * not overlap.  precision: DAFMM_FP64 or DAFMM_MIXED.  Asynchronous on stream.
+ * Calls on one ops handle must not overlap in time (they share its scratch).
+ * Errors: DAFMM_EBADARG (nrhs < 1, NULL pointers, unknown precision),
+ * DAFMM_ENOMEM (growing scratch for a larger nrhs), DAFMM_ECUDA.
+ */
+int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v_dev, double* out_dev, int precision, void* stream);
+
+/* Realised ranks, operator bytes and work of one application. */
+int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats);
+
+/*
+ * dafmm_entries -- the library's own entries K(rows[a], cols[b]) of Eq. 13,
+ * read from the device-built offset table, into out_host (nr x nc complex,
+ * interleaved, row-major).  For checking the setup against an independent
+ * quadrature.
+ */
+int dafmm_entries(const dafmm_ops* ops, long nr, const long* rows_host, long nc, const long* cols_host, double* out_host);
+
+/*
+ * dafmm_profile -- enable (1) or disable (0) CUDA-event timing of the passes
+ * of subsequent dafmm_matvec calls on this handle (events recorded on the
+ * call's stream; at most 65536 calls are kept).  Enabling clears earlier
+ * records.  dafmm_profile_read synchronises on the recorded events and sums
+ * the pass times into *out.
+ */
+int dafmm_profile(dafmm_ops* ops, int enable);
+int dafmm_profile_read(dafmm_ops* ops, dafmm_profile_t* out);
+
+/* Release an operator and its device memory.  NULL is accepted. */
+int ops_destroy(dafmm_ops* ops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAFMM_H */

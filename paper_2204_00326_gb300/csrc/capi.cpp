@@ -1,0 +1,301 @@
+// C-ABI entry points of the DAFMM library (declared in include/dafmm.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ops.h"
+
+namespace dafmm {
+namespace {
+thread_local int g_last_code = DAFMM_OK;
+thread_local std::string g_last_msg;
+}  // namespace
+
+void set_last_error(int code, const std::string& msg)
+{
+    g_last_code = code;
+    g_last_msg = msg;
+}
+
+template <typename F>
+int guarded(F&& f)
+{
+    try {
+        f();
+        set_last_error(DAFMM_OK, "");
+        return DAFMM_OK;
+    } catch (const Status& s) {
+        set_last_error(s.code, s.what());
+        return s.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error(DAFMM_ENOMEM, "host allocation failed");
+        return DAFMM_ENOMEM;
+    } catch (const std::exception& e) {
+        set_last_error(DAFMM_EBADARG, e.what());
+        return DAFMM_EBADARG;
+    }
+}
+
+void require_device()
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        fail(DAFMM_ECUDA, "no CUDA device available");
+    }
+}
+
+// Realised (unpadded) work of one application, for the roofline figures.
+void fill_stats(const Tree& t, const OpsHost& h, dafmm_stats_t& st)
+{
+    const int L = t.L;
+    double bytes_real = 0, cmacs = 0, vec = 0, c_up = 0, c_m2l = 0, c_down = 0, c_leaf = 0;
+    for (int nu = 0; nu <= L && nu < 32; nu++) {
+        if (nu < t.top) continue;
+        const Level& l = t.lv[nu];
+        const LevelOpsHost& lo = h.lv[nu];
+        long act = 0;
+        double si = 0, so = 0;
+        int mi = 0, mo = 0;
+        for (int s = 0; s < l.nslot(); s++) {
+            if (!l.active[s]) continue;
+            act++;
+            si += lo.ri[s];
+            so += lo.ro[s];
+            mi = std::max(mi, lo.ri[s]);
+            mo = std::max(mo, lo.ro[s]);
+        }
+        st.slots[nu] = act;
+        st.rank_in_max[nu] = mi;
+        st.rank_out_max[nu] = mo;
+        st.rank_in_mean[nu] = act ? si / act : 0;
+        st.rank_out_mean[nu] = act ? so / act : 0;
+        vec += 2.0 * 16.0 * (si + so);  // write + read of locals and multipoles
+        // M2L
+        for (int s = 0; s < l.nslot(); s++) {
+            if (!l.active[s]) continue;
+            for (int e = l.il_ptr[s]; e < l.il_ptr[s + 1]; e++) c_m2l += (double)lo.ri[s] * lo.ro[l.il_idx[e]];
+        }
+        // up / down transfers
+        std::vector<int> ch;
+        for (int s = 0; s < l.nslot(); s++) {
+            if (!l.active[s]) continue;
+            if (nu == L) {
+                c_up += 16.0 * lo.ro[s];
+                c_leaf += 16.0 * lo.ri[s];
+            } else {
+                child_slots(t, nu, s, ch);
+                for (int c : ch) {
+                    c_up += (double)lo.ro[s] * h.lv[nu + 1].ro[c];
+                    c_down += (double)lo.ri[s] * h.lv[nu + 1].ri[c];
+                }
+            }
+        }
+    }
+    cmacs = c_up + c_m2l + c_down + c_leaf;
+    bytes_real = cmacs * 16.0;  // every far-field operator entry is read once per application
+    const long nleaf = (long)t.nb * t.nb;
+    long p2p = 0;
+    for (int b = 0; b < nleaf; b++)
+        for (int sy = -1; sy <= 1; sy++)
+            for (int sx = -1; sx <= 1; sx++) {
+                int x = t.leaf_x[b] + sx, y = t.leaf_y[b] + sy;
+                if (x >= 0 && y >= 0 && x < t.nb && y < t.nb) p2p += 256;
+            }
+    st.p2p_cmacs_per_rhs = p2p;
+    st.cmacs_per_rhs = cmacs + (double)p2p;
+    st.operator_bytes_fp64 = bytes_real + 9 * 256 * 16.0;
+    st.operator_bytes_fp32 = bytes_real / 2 + 9 * 256 * 8.0;
+    st.vector_bytes_per_rhs = vec + (double)t.N * (16 + 16 + 8);
+    st.cmacs_up = c_up;
+    st.cmacs_m2l = c_m2l;
+    st.cmacs_down = c_down;
+    st.cmacs_leaf = c_leaf + (double)p2p;
+    st.coef_bytes_per_rhs = vec;
+    const int nlev = t.top <= L ? L - t.top + 1 : 0;
+    const int far_launches = nlev ? 1 + (nlev - 1) + nlev + (nlev - 1) : 0;
+    st.launches_per_call_fp64 = far_launches + 1;
+    st.launches_per_call = far_launches + 2;
+}
+
+}  // namespace dafmm
+
+using namespace dafmm;
+
+extern "C" {
+
+int dafmm_last_error(char* buf, size_t size)
+{
+    if (buf && size) {
+        std::snprintf(buf, size, "%s", g_last_msg.c_str());
+    }
+    return g_last_code;
+}
+
+int build_tree(const dafmm_params* params, int n_side, double x0, double x1, dafmm_tree** out)
+{
+    return guarded([&] {
+        if (!params || !out) fail(DAFMM_EBADARG, "NULL argument");
+        *out = nullptr;
+        Tree* t = make_tree(*params, n_side, x0, x1);
+        dafmm_tree* h = new dafmm_tree();
+        h->t = std::move(*t);
+        delete t;
+        *out = h;
+    });
+}
+
+int tree_nodes(const dafmm_tree* tree, double* xy)
+{
+    return guarded([&] {
+        if (!tree || !xy) fail(DAFMM_EBADARG, "NULL argument");
+        const Tree& t = tree->t;
+        double z[16];
+        cheb_nodes(t.p, z);
+        const int n2 = t.p * t.p;
+        for (long i = 0; i < t.N; i++) {
+            long leaf = i / n2;
+            int ip = (int)(i % n2);
+            double ax = t.x0 + (2.0 * t.leaf_x[leaf] + 1.0) * t.beta;
+            double ay = t.x0 + (2.0 * t.leaf_y[leaf] + 1.0) * t.beta;
+            xy[2 * i] = ax + t.beta * z[ip % t.p];
+            xy[2 * i + 1] = ay + t.beta * z[ip / t.p];
+        }
+    });
+}
+
+int tree_info(const dafmm_tree* tree, dafmm_tree_info* info)
+{
+    return guarded([&] {
+        if (!tree || !info) fail(DAFMM_EBADARG, "NULL argument");
+        const Tree& t = tree->t;
+        std::memset(info, 0, sizeof(*info));
+        info->N = t.N;
+        info->n_side = t.n_side;
+        info->levels = t.L + 1;
+        info->top = t.top;
+        for (int nu = 0; nu <= t.L && nu < 32; nu++) {
+            info->hf[nu] = t.lv[nu].hf;
+            info->cones[nu] = t.lv[nu].nc;
+            info->il_pairs[nu] = t.lv[nu].il_idx.size();
+        }
+    });
+}
+
+int tree_check(const dafmm_tree* tree, long* bad)
+{
+    return guarded([&] {
+        if (!tree || !bad) fail(DAFMM_EBADARG, "NULL argument");
+        *bad = check_tree(tree->t);
+    });
+}
+
+int tree_destroy(dafmm_tree* tree)
+{
+    delete tree;
+    return DAFMM_OK;
+}
+
+int build_nca_operators(dafmm_tree* tree, const double* q_dev, void* stream, dafmm_ops** out)
+{
+    dafmm_ops* ops = nullptr;
+    int st = guarded([&] {
+        if (!tree || !q_dev || !out) fail(DAFMM_EBADARG, "NULL argument");
+        *out = nullptr;
+        require_device();
+        const Tree& t = tree->t;
+        ops = new dafmm_ops();
+        ops->tree = tree;
+        double t_tab = build_entry_table(t, ops->table, stream);
+        OpsHost h;
+        build_nca(t, ops->table, h);
+        fill_stats(t, h, ops->stats);
+        ops->stats.setup_seconds_table = t_tab;
+        ops->stats.setup_seconds_nca = h.t_nca;
+        upload_ops(t, h, ops->dev);
+        double* q = nullptr;
+        if (cudaMalloc(&q, sizeof(double) * t.N) != cudaSuccess) {
+            cudaGetLastError();
+            fail(DAFMM_ENOMEM, "device allocation for q failed");
+        }
+        ops->dev.q = q;
+        cudaError_t e = cudaMemcpyAsync(q, q_dev, sizeof(double) * t.N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) fail(DAFMM_ECUDA, std::string("copy of q: ") + cudaGetErrorString(e));
+        *out = ops;
+    });
+    if (st != DAFMM_OK && ops) {
+        free_ops(ops->dev);
+        delete ops;
+    }
+    return st;
+}
+
+int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v, double* out, int precision, void* stream)
+{
+    return guarded([&] {
+        if (!ops || !v || !out) fail(DAFMM_EBADARG, "NULL argument");
+        if (nrhs < 1) fail(DAFMM_EBADARG, "nrhs must be >= 1");
+        if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+        if (v == out) fail(DAFMM_EBADARG, "v and out must not overlap");
+        apply_matvec(ops->tree->t, const_cast<dafmm_ops*>(ops)->dev, nrhs, v, out, precision, (cudaStream_t)stream);
+    });
+}
+
+int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats)
+{
+    return guarded([&] {
+        if (!ops || !stats) fail(DAFMM_EBADARG, "NULL argument");
+        *stats = ops->stats;
+    });
+}
+
+int dafmm_entries(const dafmm_ops* ops, long nr, const long* rows, long nc, const long* cols, double* out)
+{
+    return guarded([&] {
+        if (!ops || (nr && !rows) || (nc && !cols) || (nr && nc && !out)) fail(DAFMM_EBADARG, "NULL argument");
+        const long N = ops->tree->t.N;
+        for (long a = 0; a < nr; a++)
+            if (rows[a] < 0 || rows[a] >= N) fail(DAFMM_EBADARG, "row index out of range");
+        for (long b = 0; b < nc; b++)
+            if (cols[b] < 0 || cols[b] >= N) fail(DAFMM_EBADARG, "column index out of range");
+        for (long a = 0; a < nr; a++)
+            for (long b = 0; b < nc; b++) {
+                cd v = ops->table(rows[a], cols[b]);
+                out[2 * (a * nc + b)] = v.real();
+                out[2 * (a * nc + b) + 1] = v.imag();
+            }
+    });
+}
+
+int dafmm_profile(dafmm_ops* ops, int enable)
+{
+    return guarded([&] {
+        if (!ops) fail(DAFMM_EBADARG, "NULL argument");
+        profile_enable(ops->dev, enable != 0);
+    });
+}
+
+int dafmm_profile_read(dafmm_ops* ops, dafmm_profile_t* out)
+{
+    return guarded([&] {
+        if (!ops || !out) fail(DAFMM_EBADARG, "NULL argument");
+        profile_read(ops->dev, *out);
+    });
+}
+
+int ops_destroy(dafmm_ops* ops)
+{
+    if (!ops) return DAFMM_OK;
+    free_ops(ops->dev);
+    delete ops;
+    return DAFMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,227 @@
+"""ctypes binding of the C-ABI in ``include/dafmm.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it wraps.  Device arrays are
+torch CUDA tensors (complex128 vectors, float64 contrast); streams are torch
+CUDA streams.  A nonzero status raises :class:`DafmmError` with the library's
+message.  There is no fallback: if ``libdafmm.so`` cannot be loaded the import
+of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdafmm.so")
+
+DAFMM_OK = 0
+DAFMM_EBADARG = 1
+DAFMM_ENOMEM = 2
+DAFMM_ENOTCONV = 3
+DAFMM_EBREAKDOWN = 4
+DAFMM_ETIMEOUT = 5
+DAFMM_ECUDA = 6
+DAFMM_FP64 = 0
+DAFMM_MIXED = 1
+
+_NAMES = {0: "OK", 1: "EBADARG", 2: "ENOMEM", 3: "ENOTCONV", 4: "EBREAKDOWN", 5: "ETIMEOUT", 6: "ECUDA"}
+
+
+class DafmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"DAFMM_{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dafmm_params(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_int),
+        ("kappa", ctypes.c_double),
+        ("T", ctypes.c_double),
+        ("eps_nca", ctypes.c_double),
+        ("max_rank", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
+    ]
+
+
+class dafmm_tree_info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_long),
+        ("n_side", ctypes.c_int),
+        ("levels", ctypes.c_int),
+        ("top", ctypes.c_int),
+        ("hf", ctypes.c_int * 32),
+        ("cones", ctypes.c_int * 32),
+        ("il_pairs", ctypes.c_long * 32),
+    ]
+
+
+class dafmm_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("rank_in_max", ctypes.c_int * 32),
+        ("rank_out_max", ctypes.c_int * 32),
+        ("rank_in_mean", ctypes.c_double * 32),
+        ("rank_out_mean", ctypes.c_double * 32),
+        ("slots", ctypes.c_long * 32),
+        ("operator_bytes_fp64", ctypes.c_double),
+        ("operator_bytes_fp32", ctypes.c_double),
+        ("vector_bytes_per_rhs", ctypes.c_double),
+        ("cmacs_per_rhs", ctypes.c_double),
+        ("setup_seconds_table", ctypes.c_double),
+        ("setup_seconds_nca", ctypes.c_double),
+        ("p2p_cmacs_per_rhs", ctypes.c_long),
+        ("cmacs_up", ctypes.c_double),
+        ("cmacs_m2l", ctypes.c_double),
+        ("cmacs_down", ctypes.c_double),
+        ("cmacs_leaf", ctypes.c_double),
+        ("coef_bytes_per_rhs", ctypes.c_double),
+        ("launches_per_call", ctypes.c_int),
+        ("launches_per_call_fp64", ctypes.c_int),
+    ]
+
+
+class dafmm_profile_t(ctypes.Structure):
+    _fields_ = [
+        ("calls", ctypes.c_long),
+        ("ms_total", ctypes.c_double),
+        ("ms_up", ctypes.c_double),
+        ("ms_m2l", ctypes.c_double),
+        ("ms_down", ctypes.c_double),
+        ("ms_leaf", ctypes.c_double),
+    ]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2204_00326_gb300.build.build()")
+lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_sig = {
+    "dafmm_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "build_tree": ([ctypes.POINTER(dafmm_params), ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_P)], ctypes.c_int),
+    "tree_nodes": ([_P, _P], ctypes.c_int),
+    "tree_info": ([_P, ctypes.POINTER(dafmm_tree_info)], ctypes.c_int),
+    "tree_check": ([_P, ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
+    "tree_destroy": ([_P], ctypes.c_int),
+    "build_nca_operators": ([_P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "dafmm_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "dafmm_stats": ([_P, ctypes.POINTER(dafmm_stats_t)], ctypes.c_int),
+    "dafmm_entries": ([_P, ctypes.c_long, _P, ctypes.c_long, _P, _P], ctypes.c_int),
+    "dafmm_profile": ([_P, ctypes.c_int], ctypes.c_int),
+    "dafmm_profile_read": ([_P, ctypes.POINTER(dafmm_profile_t)], ctypes.c_int),
+    "ops_destroy": ([_P], ctypes.c_int),
+}
+EXPORTS = tuple(_sig)
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _check(st: int):
+    if st != DAFMM_OK:
+        buf = ctypes.create_string_buffer(1024)
+        lib.dafmm_last_error(buf, 1024)
+        raise DafmmError(st, buf.value.decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dptr(t, dtype_name: str) -> int:
+    import torch
+
+    if not t.is_cuda:
+        raise ValueError(f"expected a CUDA tensor of {dtype_name}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    want = {"complex128": torch.complex128, "float64": torch.float64}[dtype_name]
+    if t.dtype != want:
+        raise ValueError(f"expected dtype {want}, got {t.dtype}")
+    return int(t.data_ptr())
+
+
+def make_params(kappa: float, eps_nca: float = 1e-12, T: float = 16.0, p: int = 4, max_rank: int = 0) -> dafmm_params:
+    prm = dafmm_params()
+    prm.p = p
+    prm.kappa = kappa
+    prm.T = T
+    prm.eps_nca = eps_nca
+    prm.max_rank = max_rank
+    return prm
+
+
+def build_tree(params: dafmm_params, n_side: int, x0: float = -1.0, x1: float = 1.0) -> int:
+    h = _P()
+    _check(lib.build_tree(ctypes.byref(params), n_side, x0, x1, ctypes.byref(h)))
+    return h.value
+
+
+def tree_nodes(tree: int, N: int) -> np.ndarray:
+    xy = np.zeros((N, 2))
+    _check(lib.tree_nodes(tree, xy.ctypes.data))
+    return xy
+
+
+def tree_info(tree: int) -> dafmm_tree_info:
+    info = dafmm_tree_info()
+    _check(lib.tree_info(tree, ctypes.byref(info)))
+    return info
+
+
+def tree_check(tree: int) -> int:
+    bad = ctypes.c_long()
+    _check(lib.tree_check(tree, ctypes.byref(bad)))
+    return bad.value
+
+
+def tree_destroy(tree: int) -> None:
+    _check(lib.tree_destroy(tree))
+
+
+def build_nca_operators(tree: int, q, stream=None) -> int:
+    h = _P()
+    _check(lib.build_nca_operators(tree, _dptr(q, "float64"), _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def dafmm_matvec(ops: int, v, out, precision: int = DAFMM_FP64, stream=None) -> None:
+    nrhs = 1 if v.dim() == 1 else v.shape[1]
+    if out.shape != v.shape:
+        raise ValueError("v and out must have the same shape")
+    _check(lib.dafmm_matvec(ops, nrhs, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
+
+
+def dafmm_stats(ops: int) -> dafmm_stats_t:
+    st = dafmm_stats_t()
+    _check(lib.dafmm_stats(ops, ctypes.byref(st)))
+    return st
+
+
+def dafmm_entries(ops: int, rows, cols) -> np.ndarray:
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    cols = np.ascontiguousarray(np.asarray(cols, dtype=np.int64))
+    out = np.zeros((len(rows), len(cols), 2))
+    _check(lib.dafmm_entries(ops, len(rows), rows.ctypes.data, len(cols), cols.ctypes.data, out.ctypes.data))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def dafmm_profile(ops: int, enable: bool) -> None:
+    _check(lib.dafmm_profile(ops, 1 if enable else 0))
+
+
+def dafmm_profile_read(ops: int) -> dafmm_profile_t:
+    p = dafmm_profile_t()
+    _check(lib.dafmm_profile_read(ops, ctypes.byref(p)))
+    return p
+
+
+def ops_destroy(ops: int) -> None:
+    _check(lib.ops_destroy(ops))

@@ -1,0 +1,154 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances: FP64 mode 1e-10 relative 2-norm against the oracle's operator A
+(the DAFMM is an approximation of A to about eps_nca = 1e-12 per block, and
+the two quadratures agree to ~1e-13).  Mixed mode (complex64 operators and
+FP32 accumulation) is checked at 2e-5: complex64 rounds each stored operator
+entry to 6e-8 relative, and the realised NCA factors amplify that by the
+norms of the interpolation operators (|U|, |V| up to ~1e2), giving a few 1e-6
+on the matvec; refinement in FP64 removes it in the solver.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2204_00326_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def N():
+    import paper_2204_00326_gb300 as pkg
+
+    pkg.build()
+    from paper_2204_00326_gb300 import native
+
+    return native
+
+
+def _op(n_side, kappa, contrast, **kw):
+    from paper_2204_00326_gb300.operator import DafmmOperator
+
+    return DafmmOperator(n_side, kappa, contrast, **kw)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_entry_table_matches_oracle_entries(N):
+    w = W.GRID32_K8
+    op = _op(w.n_side, w.kappa, lambda xy: W.contrast(w, xy))
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([np.arange(16), rng.choice(w.N, 24, replace=False)])
+    Kr = O.K_rows(w.n_side, w.kappa, rows)
+    got = op.entries(rows, np.arange(w.N))
+    # self, adjacent and far leaves all appear in these rows
+    assert np.abs(got - Kr).max() < 1e-12 * np.abs(Kr).max()
+    op.close()
+
+
+@pytest.mark.parametrize("n_side,kappa", [(4, 3.0), (8, 8.0), (16, 8.0), (32, 8.0)])
+def test_fp64_matvec_matches_dense_oracle(N, n_side, kappa):
+    w = W.GRID32_K8
+    op = _op(n_side, kappa, lambda xy: W.contrast(w, xy))
+    K = O.K_dense(n_side, kappa)
+    A = O.dense_A(K, op.q, kappa)
+    for seed in (1, 2):
+        v = W.random_vector(n_side * n_side, 1, seed=seed)[:, 0]
+        out = op.matvec(torch.as_tensor(v, device="cuda"), precision=N.DAFMM_FP64).cpu().numpy()
+        assert _rel(out, A @ v) < FP64_TOL
+    # the configuration's own right-hand side: f = -kappa^2 q u_inc
+    f = -kappa ** 2 * op.q * W.plane_waves(kappa, op.xy)[:, 0]
+    out = op.matvec(torch.as_tensor(f, device="cuda"), precision=N.DAFMM_FP64).cpu().numpy()
+    assert _rel(out, A @ f) < FP64_TOL
+    op.close()
+
+
+def test_mixed_matvec_matches_dense_oracle(N):
+    w = W.GRID32_K8
+    op = _op(w.n_side, w.kappa, lambda xy: W.contrast(w, xy))
+    A = O.dense_A(O.K_dense(w.n_side, w.kappa), op.q, w.kappa)
+    v = W.random_vector(w.N, 1, seed=3)[:, 0]
+    out = op.matvec(torch.as_tensor(v, device="cuda"), precision=N.DAFMM_MIXED).cpu().numpy()
+    err = _rel(out, A @ v)
+    assert err < MIXED_TOL
+    # mixed is a different (coarser) computation, not a copy of the FP64 path
+    out64 = op.matvec(torch.as_tensor(v, device="cuda"), precision=N.DAFMM_FP64).cpu().numpy()
+    assert _rel(out64, A @ v) < err
+    op.close()
+
+
+@pytest.fixture(scope="module")
+def op128(N):
+    w = W.GRID128_K40
+    op = _op(w.n_side, w.kappa, lambda xy: W.contrast(w, xy))
+    yield op
+    op.close()
+
+
+def test_grid128_directional_tree_shape(op128):
+    info = op128.info()
+    assert info.top == 3 and info.hf[3] == 1 and info.cones[3] == 32
+    st = op128.stats()
+    assert st.slots[3] > 0 and st.rank_in_max[5] <= 16 and st.rank_out_max[5] <= 10
+
+
+def test_fp64_matvec_grid128_sampled_rows(N, op128):
+    """Full-size workload (N = 16384, directional level): sampled rows of A v."""
+    w = W.GRID128_K40
+    rng = np.random.default_rng(11)
+    rows = np.sort(rng.choice(w.N, 96, replace=False))
+    for v in (W.random_vector(w.N, 1, seed=5)[:, 0], -w.kappa ** 2 * op128.q * W.plane_waves(w.kappa, op128.xy)[:, 0]):
+        out = op128.matvec(torch.as_tensor(v, device="cuda"), precision=N.DAFMM_FP64).cpu().numpy()
+        ref = O.matvec_rows(w.n_side, w.kappa, op128.q, v, rows)
+        assert _rel(out[rows], ref) < FP64_TOL
+
+
+def test_mixed_matvec_grid128_sampled_rows(N, op128):
+    w = W.GRID128_K40
+    rows = np.sort(np.random.default_rng(12).choice(w.N, 64, replace=False))
+    v = W.random_vector(w.N, 1, seed=6)[:, 0]
+    out = op128.matvec(torch.as_tensor(v, device="cuda"), precision=N.DAFMM_MIXED).cpu().numpy()
+    ref = O.matvec_rows(w.n_side, w.kappa, op128.q, v, rows)
+    assert _rel(out[rows], ref) < MIXED_TOL
+
+
+def test_matvec_is_linear_and_repeatable(N, op128):
+    w = W.GRID128_K40
+    a = torch.as_tensor(W.random_vector(w.N, 1, seed=8)[:, 0], device="cuda")
+    b = torch.as_tensor(W.random_vector(w.N, 1, seed=9)[:, 0], device="cuda")
+    for prec in (N.DAFMM_FP64, N.DAFMM_MIXED):
+        ya = op128.matvec(a, precision=prec)
+        yb = op128.matvec(b, precision=prec)
+        yab = op128.matvec(a + 2.5j * b, precision=prec)
+        tol = 1e-13 if prec == N.DAFMM_FP64 else 1e-5
+        assert (torch.linalg.norm(yab - (ya + 2.5j * yb)) / torch.linalg.norm(yab)).item() < tol
+        assert torch.equal(op128.matvec(a, precision=prec), ya)
+
+
+def test_matvec_argument_errors(N, op128):
+    v = torch.zeros(op128.N, dtype=torch.complex128, device="cuda")
+    with pytest.raises(N.DafmmError):
+        N.dafmm_matvec(op128.ops, v, v)
+    with pytest.raises(N.DafmmError):
+        N.dafmm_matvec(op128.ops, v, torch.empty_like(v), precision=7)
+    with pytest.raises(ValueError):
+        N.dafmm_matvec(op128.ops, v.to(torch.complex64), torch.empty_like(v))
+
+
+def test_profile_records_passes(N, op128):
+    v = torch.as_tensor(W.random_vector(op128.N, 1, seed=2)[:, 0], device="cuda")
+    N.dafmm_profile(op128.ops, True)
+    for _ in range(3):
+        op128.matvec(v, precision=N.DAFMM_MIXED)
+    p = N.dafmm_profile_read(op128.ops)
+    N.dafmm_profile(op128.ops, False)
+    assert p.calls == 3 and p.ms_m2l > 0 and p.ms_leaf > 0
+    assert abs(p.ms_total - (p.ms_up + p.ms_m2l + p.ms_down + p.ms_leaf)) < 1e-6

@@ -11,7 +11,7 @@ from . import workloads  # noqa: F401
 
 def build(force: bool = False) -> str:
     """Compile libdafmm.so for sm_103a (in-tree) and return its path."""
-    from .build import build as _b
+    from .builder import build as _b
 
     return _b(force=force)
 

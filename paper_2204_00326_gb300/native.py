@@ -94,7 +94,7 @@ class dafmm_profile_t(ctypes.Structure):
 
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2204_00326_gb300.build.build()")
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2204_00326_gb300.build()")
 lib = ctypes.CDLL(LIB_PATH)
 
 _P = ctypes.c_void_p

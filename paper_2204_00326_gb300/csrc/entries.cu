@@ -11,8 +11,9 @@
 // Far offsets (max |offset| >= 2): the integrand is smooth on the square and
 // a 16 x 16 tensor Gauss-Legendre rule is used.  Near offsets: the square is
 // written as the signed sum of the four triangles (t, edge); each triangle is
-// mapped to (u, s) with y = t + u h (n + s tau) (h the signed distance from t
-// to the edge line), which puts the logarithmic singularity of Y0 at u = 0.
+// mapped to (u, s) with y = t + u (h n + s |h| tau) (h the signed distance
+// from t to the edge line, n the outward normal, tau the edge tangent), with
+// Jacobian u h |h|, which puts the logarithmic singularity of Y0 at u = 0.
 // u is integrated on geometric panels [2^-(k+1), 2^-k], s on panels graded
 // away from the foot of the perpendicular (the integrand's complex
 // singularities sit at s = +-i); 12-point Gauss-Legendre on every panel.
@@ -204,8 +205,8 @@ __global__ void near_table_kernel(int nb, double kb, double beta2, double2* tab)
             double u = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * c_nx[iu];
             double s = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * c_nx[is];
             double w = 0.25 * (u1 - u0) * (s1 - s0) * c_nw[iu] * c_nw[is];
-            double yx = tx + u * h * (nx + s * tux);
-            double yy = ty + u * h * (ny + s * tuy);
+            double yx = tx + u * (h * nx + s * ah * tux);
+            double yy = ty + u * (h * ny + s * ah * tuy);
             add_point(yx, yy, tx, ty, kb, w * u * h * ah, acc);
         }
     }

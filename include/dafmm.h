@@ -183,6 +183,33 @@ int build_nca_operators(dafmm_tree* tree, const double* q_dev, void* stream, daf
  */
 int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v_dev, double* out_dev, int precision, void* stream);
 
+/* Size of the static device scratch used by dafmm_matvec_noalloc. */
+#define DAFMM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * dafmm_matvec_noalloc -- the same application as dafmm_matvec for one
+ * right-hand side (out = A v), for callers that cannot have memory allocated
+ * on their behalf at call time: processes whose device memory is owned by
+ * their own pool, hot loops that cannot absorb cudaMalloc's implicit device
+ * synchronisation, and deployments that fix all memory up front.  The paper
+ * has no counterpart; this is a library convenience.
+ *
+ * The call allocates nothing.  Its coefficient scratch is a file-scope static
+ * device array of DAFMM_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading
+ * the library holds until the process exits.  The first call on a device
+ * resolves that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the array and clears the part it uses, so calls whose kernels
+ * overlap in time on one device race and must be ordered by the caller (one
+ * stream, or events).  The operator itself (built by build_nca_operators)
+ * must already exist; v_dev and out_dev are the caller's N complex128 device
+ * vectors and must not overlap.
+ * Errors: DAFMM_EBADARG when the problem needs more scratch than the array
+ * holds (the message states both sizes), for NULL pointers or an unknown
+ * precision; DAFMM_ECUDA for CUDA errors.
+ */
+int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v_dev, double* out_dev, int precision, void* stream);
+
 /* Realised ranks, operator bytes and work of one application. */
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats);
 

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "ops.h"
@@ -431,6 +432,105 @@ void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* o
         run<double>(t, d, v, out, stream);
     else
         run<float>(t, d, v, out, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free application.  Some callers cannot let the library allocate
+// device memory at call time: processes whose device memory is owned by their
+// own pool (a cudaMalloc there can fail or fragment the pool), hot loops that
+// cannot afford cudaMalloc's implicit device synchronisation, and deployments
+// that must fix all memory before they start.  For them the coefficient
+// scratch of one single-RHS application lives in this fixed device array
+// instead of the handle's grow-on-demand buffers.  Every GPU that loads the
+// library holds the array until the process exits; all calls on a device
+// share it, so calls whose kernels overlap in time on that device race.
+namespace {
+
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DAFMM_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device.  The first call
+// on a device resolves it with cudaGetSymbolAddress (this set-up should happen
+// before any stream capture); later calls reuse the cached address.
+unsigned char* noalloc_scratch()
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(DAFMM_EBADARG, "device ordinal out of range for the static scratch");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            fail(DAFMM_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    return (unsigned char*)g_noalloc_addr[dev];
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <typename T>
+void run_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, cudaStream_t s)
+{
+    using C = typename V2<T>::t;
+    const int L = t.L;
+    const long N = t.N;
+    const int nleaf = t.nb * t.nb;
+    const bool far = t.top <= L;
+    void* mp[64] = {};
+    void* lc[64] = {};
+    if (L >= 64) fail(DAFMM_EBADARG, "tree too deep for the allocation-free path");
+    // carve the scratch: complex64 copy of v (mixed), then per level multipoles and locals
+    size_t need = sizeof(T) == 4 ? align256(sizeof(float2) * (size_t)N) : 0;
+    if (far)
+        for (int nu = t.top; nu <= L; nu++)
+            need += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ro) +
+                    align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ri);
+    if (need > (size_t)DAFMM_NOALLOC_SCRATCH_BYTES)
+        fail(DAFMM_EBADARG, "problem needs " + std::to_string(need) + " bytes of scratch; the allocation-free path holds " +
+                                std::to_string((size_t)DAFMM_NOALLOC_SCRATCH_BYTES) + " (use dafmm_matvec)");
+    unsigned char* base = noalloc_scratch();
+    // the array keeps the previous call's contents: start from zeros
+    CK(cudaMemsetAsync(base, 0, need, s));
+    size_t off = 0;
+    const C* vin = (const C*)v;
+    if (sizeof(T) == 4) {
+        float2* v32 = (float2*)(base + off);
+        off += align256(sizeof(float2) * (size_t)N);
+        to_c64_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, (const double2*)v, v32);
+        vin = (const C*)v32;
+    }
+    if (far) {
+        for (int nu = t.top; nu <= L; nu++) {
+            mp[nu] = base + off;
+            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ro);
+            lc[nu] = base + off;
+            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ri);
+        }
+        launch_bsr<T>(d.lv[L].up, vin, 16, mp[L], d.lv[L].Ro, 0, s);
+        for (int nu = L - 1; nu >= t.top; nu--) launch_bsr<T>(d.lv[nu].up, mp[nu + 1], d.lv[nu + 1].Ro, mp[nu], d.lv[nu].Ro, 0, s);
+        for (int nu = t.top; nu <= L; nu++) launch_bsr<T>(d.lv[nu].m2l, mp[nu], d.lv[nu].Ro, lc[nu], d.lv[nu].Ri, 0, s);
+        for (int nu = t.top; nu < L; nu++) launch_bsr<T>(d.lv[nu].down, lc[nu], d.lv[nu].Ri, lc[nu + 1], d.lv[nu + 1].Ri, 1, s);
+    }
+    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
+    const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
+    leaf_apply_kernel<T><<<(unsigned)((nleaf + 7) / 8), 128, 0, s>>>(
+        nleaf, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr,
+        far ? d.lv[L].Ri : 0, far ? (const C*)lc[L] : nullptr, (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
+    CK(cudaGetLastError());
+}
+
+}  // namespace
+
+void apply_matvec_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream)
+{
+    if (precision == DAFMM_FP64)
+        run_noalloc<double>(t, d, v, out, stream);
+    else
+        run_noalloc<float>(t, d, v, out, stream);
 }
 
 }  // namespace dafmm

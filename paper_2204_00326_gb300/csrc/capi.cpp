@@ -248,6 +248,16 @@ int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v, double* out, i
     });
 }
 
+int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v, double* out, int precision, void* stream)
+{
+    return guarded([&] {
+        if (!ops || !v || !out) fail(DAFMM_EBADARG, "NULL argument");
+        if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+        if (v == out) fail(DAFMM_EBADARG, "v and out must not overlap");
+        apply_matvec_noalloc(ops->tree->t, ops->dev, v, out, precision, (cudaStream_t)stream);
+    });
+}
+
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats)
 {
     return guarded([&] {

@@ -44,6 +44,8 @@ void profile_read(OpsDev& d, dafmm_profile_t& p);
 void ensure_scratch(const Tree& t, OpsDev& d, int nrhs);
 // out = v + kappa^2 q (K~ v), asynchronous on stream.
 void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream);
+// Same operator, one right-hand side, scratch in a static device array.
+void apply_matvec_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream);
 
 }  // namespace dafmm
 

@@ -107,6 +107,7 @@ _sig = {
     "tree_destroy": ([_P], ctypes.c_int),
     "build_nca_operators": ([_P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "dafmm_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_stats": ([_P, ctypes.POINTER(dafmm_stats_t)], ctypes.c_int),
     "dafmm_entries": ([_P, ctypes.c_long, _P, ctypes.c_long, _P, _P], ctypes.c_int),
     "dafmm_profile": ([_P, ctypes.c_int], ctypes.c_int),
@@ -197,6 +198,17 @@ def dafmm_matvec(ops: int, v, out, precision: int = DAFMM_FP64, stream=None) -> 
     if out.shape != v.shape:
         raise ValueError("v and out must have the same shape")
     _check(lib.dafmm_matvec(ops, nrhs, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def dafmm_matvec_noalloc(ops: int, v, out, precision: int = DAFMM_FP64, stream=None) -> None:
+    """dafmm_matvec for one right-hand side with the library's static scratch
+    (for callers that cannot allocate device memory at call time)."""
+    if v.dim() != 1 or out.shape != v.shape:
+        raise ValueError("one right-hand side: v and out are (N,) vectors")
+    _check(lib.dafmm_matvec_noalloc(ops, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
 
 
 def dafmm_stats(ops: int) -> dafmm_stats_t:

@@ -210,6 +210,15 @@ int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v_dev, double* ou
  */
 int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v_dev, double* out_dev, int precision, void* stream);
 
+/*
+ * dafmm_sync -- synchronise the stream, then report whether any kernel of
+ * this handle gave up a bounded wait on a device-side barrier since the last
+ * check (DAFMM_ETIMEOUT; the flag is cleared).  Otherwise DAFMM_OK, or
+ * DAFMM_ECUDA for a CUDA error.  The apply kernels wait on the arrival of
+ * their own bulk copies with an iteration limit instead of an unbounded spin.
+ */
+int dafmm_sync(dafmm_ops* ops, void* stream);
+
 /* Realised ranks, operator bytes and work of one application. */
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats);
 

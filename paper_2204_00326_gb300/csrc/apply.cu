@@ -2,15 +2,27 @@
 //
 // Every tree pass is a block-sparse complex matrix-vector product between
 // coefficient spaces (P2M, M2M and directional M2M up; M2L and directional
-// M2L across; directional L2L, L2L down).  One kernel serves them all: a warp
-// owns one output row (a box, or a (box, cone) slot), streams that row's
-// operator blocks once from HBM with coalesced loads, gathers the input
-// coefficients of the listed slots, and accumulates in registers; lanes split
-// the inner index when blocks are narrower than a warp and reduce by
-// shuffles.  The leaf kernel fuses L2P, the tabulated near field (nine shared
-// 16 x 16 blocks kept in shared memory) and the epilogue v + kappa^2 q (.).
+// M2L across; directional L2L, L2L down).  The blocks of one output row are
+// stored contiguously at their realised NCA ranks, so a row is one
+// rout x J column-major matrix, read exactly once per application: the
+// single-right-hand-side apply is bound by HBM bandwidth (complex64) or by
+// the FP64 pipes (complex128).
+//
+// Streaming: rows are cut into column ranges ("chunks") of about 1536
+// entries.  Each warp runs a two-stage pipeline: one lane issues a TMA bulk
+// copy (cp.async.bulk, completion on an mbarrier) of the next chunk's matrix
+// into shared memory while the warp gathers the chunk's input coefficients
+// and multiplies the current stage (lanes cover the output index and, for
+// narrow blocks, interleave the columns).  Every mbarrier wait is bounded; on
+// timeout the kernel raises a device error flag, drains its own copy in
+// flight and returns.  A chunk that is its row's only chunk writes the row;
+// otherwise it writes a partial that a second kernel adds in a fixed order,
+// so results are bit-reproducible.  The M2L of all levels is one launch.
+// The leaf kernel fuses L2P, the tabulated near field (nine shared 16 x 16
+// blocks in shared memory) and the epilogue v + kappa^2 q (.).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -31,91 +43,423 @@ struct V2<float> {
     using t = float2;
 };
 
-constexpr int kRowsPerCta = 4;   // one warp per output row
-constexpr int kMaxChunks = 4;    // output blocks up to 128 rows
+constexpr int kWarpsPerCta = 8;
+constexpr int kMaxPass = 12;        // passes in one launch group
+constexpr long kChunkElems = 1024;  // matrix entries per chunk (8 KB in complex64)
 
-// y[row] (+)= sum_e M_e x[col_e]; M_e is Rout x Rin, column-major.
 template <typename T>
-__global__ void __launch_bounds__(128) bsr_apply_kernel(int nrows, const int* __restrict__ rowptr, const int* __restrict__ col,
-                                                        const typename V2<T>::t* __restrict__ mats, int Rout, int Rin,
-                                                        const typename V2<T>::t* __restrict__ x, int ldx,
-                                                        typename V2<T>::t* __restrict__ y, int ldy, int accumulate)
+struct PassArgs {
+    const int* rout;    // per row
+    const long* rbase;  // per row: element offset of the row's matrix in mats
+    const int* cbase;   // per row: offset of the row's columns in xmap
+    const int* xmap;    // per column: index of its input coefficient in x
+    const typename V2<T>::t* mats;
+    const typename V2<T>::t* x;
+    typename V2<T>::t* y;
+    int ldy;
+};
+
+template <typename T>
+struct GroupArgs {
+    PassArgs<T> p[kMaxPass];
+};
+
+template <typename T>
+__device__ __forceinline__ void cmac(T& ar, T& ai, typename V2<T>::t m, typename V2<T>::t x)
+{
+    ar = fma(m.x, x.x, fma(-m.y, x.y, ar));
+    ai = fma(m.x, x.y, fma(m.y, x.x, ai));
+}
+
+constexpr int kMaxChunkCols = 128;   // columns per chunk (shared gather buffer)
+constexpr int kStreamWarps = 4;      // warps per CTA, each with its own pipeline
+constexpr long kSpinLimit = 1L << 22;  // bounded mbarrier waits
+
+template <typename T>
+struct StreamCfg {
+    using C = typename V2<T>::t;
+    static constexpr int kStage = ((int)(kChunkElems * sizeof(C)) + 32 + 127) / 128 * 128;
+    static constexpr int kXs = kMaxChunkCols * (int)sizeof(C);
+    static constexpr int kWarp = 2 * kStage + kXs + 128;  // two stages, gather buffer, barriers
+    static constexpr int kCta = kStreamWarps * kWarp;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Arm the barrier for bytes and start one bulk copy global -> shared.
+__device__ __forceinline__ void tma_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Wait for the barrier's phase with the given parity; false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (long k = 0; k < kSpinLimit; k++) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// A chunk record is two int4: a = {pass | direct << 8 | rout << 16, row,
+// ncol, first xmap index}, b = {element offset of the chunk's matrix (lo, hi),
+// entries, first chunk of the row}.  The matrix of a chunk is ld x ncol
+// (ld = rout rounded up to even) and starts at an even element, so its bytes
+// start 16-byte aligned.
+constexpr int kMaxPrefetch = kMaxChunkCols / 32;
+
+template <typename T>
+__device__ __forceinline__ const char* chunk_src(const GroupArgs<T>& g, const int4& a, const int4& b, unsigned& bytes)
 {
     using C = typename V2<T>::t;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kRowsPerCta + warp;
-    if (row >= nrows) return;
-    const int e0 = rowptr[row], e1 = rowptr[row + 1];
-    const size_t blk = (size_t)Rin * Rout;
-    if (Rout <= 32) {
-        // Rout in {8, 16, 32}: lane = i + Rout * jp
-        const int i = lane % Rout, jp = lane / Rout, JP = 32 / Rout;
-        T ar = 0, ai = 0;
-        for (int e = e0; e < e1; e++) {
-            const C* M = mats + (size_t)e * blk + i;
-            const C* xv = x + (size_t)col[e] * ldx;
-#pragma unroll 4
-            for (int j = jp; j < Rin; j += JP) {
-                C m = M[(size_t)j * Rout];
-                C xx = xv[j];
-                ar = fma(m.x, xx.x, fma(-m.y, xx.y, ar));
-                ai = fma(m.x, xx.y, fma(m.y, xx.x, ai));
+    const PassArgs<T>& pa = g.p[a.x & 0xff];
+    const long elem = (long)(unsigned)b.x | ((long)b.y << 32);
+    bytes = (unsigned)((size_t)b.z * sizeof(C));
+    return (const char*)(pa.mats + elem);
+}
+
+// Load (into registers) the input coefficients of the chunk described by a.
+template <typename T>
+__device__ __forceinline__ void gather_x(const GroupArgs<T>& g, const int4& a, int lane, typename V2<T>::t* xr)
+{
+    const PassArgs<T>& pa = g.p[a.x & 0xff];
+#pragma unroll
+    for (int k = 0; k < kMaxPrefetch; k++) {
+        const int t = lane + 32 * k;
+        if (t < a.z) xr[k] = pa.x[pa.xmap[a.w + t]];
+    }
+}
+
+// Per-lane accumulators of one output row: 4 slots x (re, im), two
+// independent sets (A for even, B for odd column steps).
+template <typename T>
+struct Acc {
+    T r[2][4], i[2][4];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) r[s][k] = i[s][k] = 0;
+    }
+};
+
+// Multiply one chunk held in shared memory into the accumulators.
+// complex64: lane handles row pairs (2p, 2p+1) with 16-byte loads, p = lane %
+// NP (+32); complex128: lane handles rows i = lane % ro (+32k).  When the
+// rows fit in fewer than 32 lanes, lane groups jp interleave the columns.
+template <typename T>
+__device__ __forceinline__ void chunk_mac(Acc<T>& acc, const typename V2<T>::t* M, const typename V2<T>::t* xs, int ro, int ld,
+                                          int ncol, int lane)
+{
+    if constexpr (sizeof(T) == 4) {
+        const int NP = (ro + 1) >> 1;
+        if (NP <= 32) {
+            const int JP = 32 / NP, p = lane % NP, jp = lane / NP;
+            if (jp >= JP) return;
+            const float4* M4 = (const float4*)(M) + p;
+            const int ld2 = ld >> 1;
+            int j = jp;
+#pragma unroll 2
+            for (; j + JP < ncol; j += 2 * JP) {
+                const float4 m0 = M4[j * ld2], m1 = M4[(j + JP) * ld2];
+                const float2 x0 = xs[j], x1 = xs[j + JP];
+                acc.r[0][0] = fmaf(m0.x, x0.x, fmaf(-m0.y, x0.y, acc.r[0][0]));
+                acc.i[0][0] = fmaf(m0.x, x0.y, fmaf(m0.y, x0.x, acc.i[0][0]));
+                acc.r[0][1] = fmaf(m0.z, x0.x, fmaf(-m0.w, x0.y, acc.r[0][1]));
+                acc.i[0][1] = fmaf(m0.z, x0.y, fmaf(m0.w, x0.x, acc.i[0][1]));
+                acc.r[1][0] = fmaf(m1.x, x1.x, fmaf(-m1.y, x1.y, acc.r[1][0]));
+                acc.i[1][0] = fmaf(m1.x, x1.y, fmaf(m1.y, x1.x, acc.i[1][0]));
+                acc.r[1][1] = fmaf(m1.z, x1.x, fmaf(-m1.w, x1.y, acc.r[1][1]));
+                acc.i[1][1] = fmaf(m1.z, x1.y, fmaf(m1.w, x1.x, acc.i[1][1]));
             }
-        }
-        for (int o = Rout; o < 32; o <<= 1) {
-            ar += __shfl_xor_sync(0xffffffffu, ar, o);
-            ai += __shfl_xor_sync(0xffffffffu, ai, o);
-        }
-        if (jp == 0) {
-            C* yy = y + (size_t)row * ldy + i;
-            if (accumulate) {
-                C o = *yy;
-                ar += o.x;
-                ai += o.y;
+            if (j < ncol) {
+                const float4 m0 = M4[j * ld2];
+                const float2 x0 = xs[j];
+                acc.r[0][0] = fmaf(m0.x, x0.x, fmaf(-m0.y, x0.y, acc.r[0][0]));
+                acc.i[0][0] = fmaf(m0.x, x0.y, fmaf(m0.y, x0.x, acc.i[0][0]));
+                acc.r[0][1] = fmaf(m0.z, x0.x, fmaf(-m0.w, x0.y, acc.r[0][1]));
+                acc.i[0][1] = fmaf(m0.z, x0.y, fmaf(m0.w, x0.x, acc.i[0][1]));
             }
-            C r;
-            r.x = ar;
-            r.y = ai;
-            *yy = r;
+        } else {
+            const float4* M4 = (const float4*)(M);
+            const int ld2 = ld >> 1;
+            const bool second = lane + 32 < NP;
+#pragma unroll 2
+            for (int j = 0; j < ncol; j++) {
+                const float2 x0 = xs[j];
+                const float4 m0 = M4[j * ld2 + lane];
+                acc.r[0][0] = fmaf(m0.x, x0.x, fmaf(-m0.y, x0.y, acc.r[0][0]));
+                acc.i[0][0] = fmaf(m0.x, x0.y, fmaf(m0.y, x0.x, acc.i[0][0]));
+                acc.r[0][1] = fmaf(m0.z, x0.x, fmaf(-m0.w, x0.y, acc.r[0][1]));
+                acc.i[0][1] = fmaf(m0.z, x0.y, fmaf(m0.w, x0.x, acc.i[0][1]));
+                if (second) {
+                    const float4 m1 = M4[j * ld2 + lane + 32];
+                    acc.r[0][2] = fmaf(m1.x, x0.x, fmaf(-m1.y, x0.y, acc.r[0][2]));
+                    acc.i[0][2] = fmaf(m1.x, x0.y, fmaf(m1.y, x0.x, acc.i[0][2]));
+                    acc.r[0][3] = fmaf(m1.z, x0.x, fmaf(-m1.w, x0.y, acc.r[0][3]));
+                    acc.i[0][3] = fmaf(m1.z, x0.y, fmaf(m1.w, x0.x, acc.i[0][3]));
+                }
+            }
         }
     } else {
-        const int nch = (Rout + 31) / 32;
-        T ar[kMaxChunks], ai[kMaxChunks];
+        if (ro <= 32) {
+            const int JP = 32 / ro, i = lane % ro, jp = lane / ro;
+            if (jp >= JP) return;
+            const double2* Mi = M + i;
+            int j = jp;
+#pragma unroll 2
+            for (; j + JP < ncol; j += 2 * JP) {
+                const double2 m0 = Mi[j * ld], m1 = Mi[(j + JP) * ld];
+                const double2 x0 = xs[j], x1 = xs[j + JP];
+                acc.r[0][0] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][0]));
+                acc.i[0][0] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][0]));
+                acc.r[1][0] = fma(m1.x, x1.x, fma(-m1.y, x1.y, acc.r[1][0]));
+                acc.i[1][0] = fma(m1.x, x1.y, fma(m1.y, x1.x, acc.i[1][0]));
+            }
+            if (j < ncol) {
+                const double2 m0 = Mi[j * ld];
+                const double2 x0 = xs[j];
+                acc.r[0][0] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][0]));
+                acc.i[0][0] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][0]));
+            }
+        } else {
+            const int nck = (ro + 31) / 32;
+#pragma unroll 2
+            for (int j = 0; j < ncol; j++) {
+                const double2 x0 = xs[j];
 #pragma unroll
-        for (int c = 0; c < kMaxChunks; c++) ar[c] = ai[c] = 0;
-        for (int e = e0; e < e1; e++) {
-            const C* M = mats + (size_t)e * blk;
-            const C* xv = x + (size_t)col[e] * ldx;
-            for (int j = 0; j < Rin; j++) {
-                C xx = xv[j];
+                for (int k = 0; k < 4; k++)
+                    if (k < nck && k * 32 + lane < ro) {
+                        const double2 m = M[j * ld + k * 32 + lane];
+                        acc.r[0][k] = fma(m.x, x0.x, fma(-m.y, x0.y, acc.r[0][k]));
+                        acc.i[0][k] = fma(m.x, x0.y, fma(m.y, x0.x, acc.i[0][k]));
+                    }
+            }
+        }
+    }
+}
+
+// Sum the accumulators over the lane groups and write the row (to y when the
+// chunk range covers the whole row, else to the partial slot P[pslot]).
+template <typename T>
+__device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typename V2<T>::t* dst, bool to_y, int accumulate)
+{
+    using C = typename V2<T>::t;
+    // combine the two independent sets
 #pragma unroll
-                for (int c = 0; c < kMaxChunks; c++) {
-                    int i = c * 32 + lane;
-                    if (c < nch && i < Rout) {
-                        C m = M[(size_t)j * Rout + i];
-                        ar[c] = fma(m.x, xx.x, fma(-m.y, xx.y, ar[c]));
-                        ai[c] = fma(m.x, xx.y, fma(m.y, xx.x, ai[c]));
+    for (int k = 0; k < 4; k++) {
+        acc.r[0][k] += acc.r[1][k];
+        acc.i[0][k] += acc.i[1][k];
+    }
+    auto put = [&](int row, T re, T im) {
+        C* q = dst + row;
+        if (to_y && accumulate) {
+            const C o = *q;
+            re += o.x;
+            im += o.y;
+        }
+        C r;
+        r.x = re;
+        r.y = im;
+        *q = r;
+    };
+    if constexpr (sizeof(T) == 4) {
+        const int NP = (ro + 1) >> 1;
+        if (NP <= 32) {
+            const int JP = 32 / NP, p = lane % NP, jp = lane / NP;
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+                for (int q = 1; q < JP; q++) {
+                    const int src = (lane + q * NP) & 31;
+                    const float tr = __shfl_sync(0xffffffffu, acc.r[0][k], src);
+                    const float ti = __shfl_sync(0xffffffffu, acc.i[0][k], src);
+                    if (jp == 0) {
+                        acc.r[0][k] += tr;
+                        acc.i[0][k] += ti;
                     }
                 }
+            if (jp == 0) {
+                put(2 * p, acc.r[0][0], acc.i[0][0]);
+                if (2 * p + 1 < ro) put(2 * p + 1, acc.r[0][1], acc.i[0][1]);
+            }
+        } else {
+            put(2 * lane, acc.r[0][0], acc.i[0][0]);
+            if (2 * lane + 1 < ro) put(2 * lane + 1, acc.r[0][1], acc.i[0][1]);
+            if (lane + 32 < NP) {
+                put(2 * lane + 64, acc.r[0][2], acc.i[0][2]);
+                if (2 * lane + 65 < ro) put(2 * lane + 65, acc.r[0][3], acc.i[0][3]);
             }
         }
-#pragma unroll
-        for (int c = 0; c < kMaxChunks; c++) {
-            int i = c * 32 + lane;
-            if (c < nch && i < Rout) {
-                C* yy = y + (size_t)row * ldy + i;
-                T rr = ar[c], ri = ai[c];
-                if (accumulate) {
-                    C o = *yy;
-                    rr += o.x;
-                    ri += o.y;
+    } else {
+        if (ro <= 32) {
+            const int JP = 32 / ro, i = lane % ro, jp = lane / ro;
+            for (int q = 1; q < JP; q++) {
+                const int src = (lane + q * ro) & 31;
+                const double tr = __shfl_sync(0xffffffffu, acc.r[0][0], src);
+                const double ti = __shfl_sync(0xffffffffu, acc.i[0][0], src);
+                if (jp == 0) {
+                    acc.r[0][0] += tr;
+                    acc.i[0][0] += ti;
                 }
-                C r;
-                r.x = rr;
-                r.y = ri;
-                *yy = r;
             }
+            if (jp == 0) put(i, acc.r[0][0], acc.i[0][0]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (k * 32 + lane < ro) put(k * 32 + lane, acc.r[0][k], acc.i[0][k]);
         }
+    }
+}
+
+// Each warp streams a contiguous range of kpw chunks through a two-stage
+// TMA pipeline and accumulates consecutive chunks of one row in registers.
+// A row's result goes to y when its only chunk is in this range and the row
+// has no other chunk (direct), else to P at the first chunk this warp
+// processed for the row (the reduction knows those slots from kpw).
+template <typename T>
+__global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(int nch, int kpw, const int4* __restrict__ recs,
+                                                                   const __grid_constant__ GroupArgs<T> g,
+                                                                   typename V2<T>::t* __restrict__ P, int Pld, int accumulate,
+                                                                   int* __restrict__ err)
+{
+    using C = typename V2<T>::t;
+    using Cfg = StreamCfg<T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* wb = smem + (size_t)warp * Cfg::kWarp;
+    auto stage = [&](int k) { return (C*)(wb + (size_t)k * Cfg::kStage); };
+    C* xs = (C*)(wb + 2 * Cfg::kStage);
+    unsigned long long* bar = (unsigned long long*)(wb + 2 * Cfg::kStage + Cfg::kXs);
+    const int wg = blockIdx.x * kStreamWarps + warp;
+    const int cb = wg * kpw;
+    const int ce = min(nch, cb + kpw);
+    if (cb >= ce) return;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int k = 0; k < 2 && cb + k < ce; k++) {
+            unsigned bytes;
+            const char* src = chunk_src<T>(g, recs[2 * (cb + k)], recs[2 * (cb + k) + 1], bytes);
+            tma_load(stage(k), src, bytes, &bar[k]);
+        }
+    }
+    __syncwarp();
+    int4 ra = recs[2 * cb], rb = recs[2 * cb + 1];
+    C xr[kMaxPrefetch];
+    gather_x<T>(g, ra, lane, xr);
+    Acc<T> acc;
+    acc.zero();
+    int pslot = cb;  // first chunk of the current row in this range
+    for (int c = cb, it = 0; c < ce; c++, it++) {
+        const int s = it & 1;
+        const unsigned parity = (unsigned)((it >> 1) & 1);
+        // commit this chunk's inputs, then start loading the next chunk's
+        const int ncol = ra.z;
+#pragma unroll
+        for (int k = 0; k < kMaxPrefetch; k++) {
+            const int t = lane + 32 * k;
+            if (t < ncol) xs[t] = xr[k];
+        }
+        int4 na = make_int4(-1, -1, 0, 0), nb = make_int4(0, 0, 0, 0);
+        if (c + 1 < ce) {
+            na = recs[2 * (c + 1)];
+            nb = recs[2 * (c + 1) + 1];
+            gather_x<T>(g, na, lane, xr);
+        }
+        int4 fa = make_int4(0, 0, 0, 0), fb = make_int4(0, 0, 0, 0);
+        if (lane == 0 && c + 2 < ce) {
+            fa = recs[2 * (c + 2)];
+            fb = recs[2 * (c + 2) + 1];
+        }
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar[s], parity));
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(err, 1);
+                // copies of this warp may still be in flight: give both stages a
+                // bounded chance to land before the shared memory is released
+                mbar_wait(&bar[s], parity);
+                if (c + 1 < ce) mbar_wait(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+            }
+            __syncwarp();
+            return;
+        }
+        __syncwarp();
+        const PassArgs<T>& pa = g.p[ra.x & 0xff];
+        const int ro = (ra.x >> 16) & 0xffff;
+        const int ld = ro + (ro & 1);
+        chunk_mac<T>(acc, stage(s), xs, ro, ld, ncol, lane);
+        // every lane is done with this stage and the gather buffer: refill the stage
+        __syncwarp();
+        if (lane == 0 && c + 2 < ce) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            unsigned nbytes;
+            const char* src = chunk_src<T>(g, fa, fb, nbytes);
+            tma_load(stage(s), src, nbytes, &bar[s]);
+        }
+        // end of this row's run in the range: write it out
+        const bool row_ends = (c + 1 == ce) || na.x != ra.x || na.y != ra.y;
+        if (row_ends) {
+            const bool direct = (ra.x >> 8) & 1;
+            C* dst = direct ? pa.y + (size_t)ra.y * pa.ldy : P + (size_t)pslot * Pld;
+            flush_row<T>(acc, ro, lane, dst, direct, accumulate);
+            acc.zero();
+            pslot = c + 1;
+        }
+        ra = na;
+        rb = nb;
+    }
+}
+
+// One warp per row {pass, row, c0, c1}: y[row] (+)= the row's partials, in
+// chunk order.  Partials sit at the row's first chunk c0 and at every chunk
+// k * kpw (the first chunk of a warp's range) inside (c0, c1).
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) reduce_kernel(int nrows, int kpw, const int4* __restrict__ rows,
+                                                                   const __grid_constant__ GroupArgs<T> g,
+                                                                   const typename V2<T>::t* __restrict__ P, int Pld,
+                                                                   int accumulate)
+{
+    using C = typename V2<T>::t;
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    if (w >= nrows) return;
+    const int4 r = rows[w];
+    const PassArgs<T>& pa = g.p[r.x & 0xff];
+    const int ro = pa.rout[r.y];
+    C* y = pa.y + (size_t)r.y * pa.ldy;
+    for (int i = lane; i < ro; i += 32) {
+        T sr = 0, si = 0;
+        if (accumulate) {
+            C o = y[i];
+            sr = o.x;
+            si = o.y;
+        }
+        for (int c = r.z; c < r.w; c = (c / kpw + 1) * kpw) {
+            C p = P[(size_t)c * Pld + i];
+            sr += p.x;
+            si += p.y;
+        }
+        C o;
+        o.x = sr;
+        o.y = si;
+        y[i] = o;
     }
 }
 
@@ -126,8 +470,9 @@ template <typename T>
 __global__ void __launch_bounds__(128) leaf_apply_kernel(int nleaf, const int* __restrict__ nbr,
                                                          const typename V2<T>::t* __restrict__ near,
                                                          const typename V2<T>::t* __restrict__ vin,
-                                                         const int* __restrict__ l2p_rowptr,
-                                                         const typename V2<T>::t* __restrict__ l2p, int Ri,
+                                                         const int* __restrict__ l2p_rowptr, const long* __restrict__ l2p_moff,
+                                                         const int* __restrict__ l2p_rin,
+                                                         const typename V2<T>::t* __restrict__ l2p, int ldl,
                                                          const typename V2<T>::t* __restrict__ lc,
                                                          const double2* __restrict__ v, const double* __restrict__ q, double k2,
                                                          double2* __restrict__ out)
@@ -147,28 +492,19 @@ __global__ void __launch_bounds__(128) leaf_apply_kernel(int nleaf, const int* _
         const C* vs = vin + (size_t)src * 16;
         const C* B = sn + o * 256 + i;
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            C m = B[j * 16];
-            C xx = vs[j];
-            ar = fma(m.x, xx.x, fma(-m.y, xx.y, ar));
-            ai = fma(m.x, xx.y, fma(m.y, xx.x, ai));
-        }
+        for (int j = 0; j < 16; j++) cmac<T>(ar, ai, B[j * 16], vs[j]);
     }
     if (l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {
         const int e = l2p_rowptr[leaf];
-        const C* U = l2p + (size_t)e * Ri * 16 + i;
-        const C* u = lc + (size_t)leaf * Ri;
-        for (int j = 0; j < Ri; j++) {
-            C m = U[j * 16];
-            C xx = u[j];
-            ar = fma(m.x, xx.x, fma(-m.y, xx.y, ar));
-            ai = fma(m.x, xx.y, fma(m.y, xx.x, ai));
-        }
+        const C* U = l2p + l2p_moff[e] + i;
+        const C* u = lc + (size_t)leaf * ldl;
+        const int ri = l2p_rin[e];
+        for (int j = 0; j < ri; j++) cmac<T>(ar, ai, U[j * 16], u[j]);
     }
-    const size_t g = (size_t)leaf * 16 + i;
-    const double2 vv = v[g];
-    const double s = k2 * q[g];
-    out[g] = make_double2(vv.x + s * (double)ar, vv.y + s * (double)ai);
+    const size_t gi = (size_t)leaf * 16 + i;
+    const double2 vv = v[gi];
+    const double s = k2 * q[gi];
+    out[gi] = make_double2(vv.x + s * (double)ar, vv.y + s * (double)ai);
 }
 
 __global__ void to_c64_kernel(long n, const double2* __restrict__ a, float2* __restrict__ b)
@@ -180,7 +516,10 @@ __global__ void to_c64_kernel(long n, const double2* __restrict__ a, float2* __r
 #define CK(x)                                                                                     \
     do {                                                                                          \
         cudaError_t e_ = (x);                                                                     \
-        if (e_ != cudaSuccess) fail(DAFMM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGetLastError(); /* do not leave the error for a later check */                    \
+            fail(DAFMM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));                   \
+        }                                                                                         \
     } while (0)
 
 template <typename P>
@@ -196,20 +535,31 @@ void dev_alloc(P** p, size_t bytes)
     }
 }
 
+template <typename V>
+void upload_vec(const std::vector<V>& h, V** d)
+{
+    dev_alloc(d, sizeof(V) * h.size());
+    if (!h.empty()) CK(cudaMemcpy(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice));
+}
+
 void upload_bsr(BsrHost& h, BsrDev& d)
 {
     d.nrows = h.nrows;
     d.Rout = h.Rout;
     d.Rin = h.Rin;
     d.nnz = h.nnz();
-    if (h.Rout > 32 * kMaxChunks) fail(DAFMM_EBADARG, "rank above 128; set max_rank or loosen eps_nca");
-    dev_alloc(&d.rowptr, sizeof(int) * (h.nrows + 1));
-    CK(cudaMemcpy(d.rowptr, h.rowptr.data(), sizeof(int) * (h.nrows + 1), cudaMemcpyHostToDevice));
-    dev_alloc(&d.col, sizeof(int) * h.col.size());
-    if (!h.col.empty()) CK(cudaMemcpy(d.col, h.col.data(), sizeof(int) * h.col.size(), cudaMemcpyHostToDevice));
+    d.nelem = (long)h.mats.size();
+    upload_vec(h.rowptr, &d.rowptr);
+    upload_vec(h.rout, &d.rout);
+    upload_vec(h.col, &d.col);
+    upload_vec(h.rin, &d.rin);
+    upload_vec(h.moff, &d.moff);
     const size_t n = h.mats.size();
-    dev_alloc((double2**)&d.m64, sizeof(double2) * n);
-    dev_alloc((float2**)&d.m32, sizeof(float2) * n);
+    // two spare entries: a bulk copy rounds its window out to 16-byte words
+    dev_alloc((double2**)&d.m64, sizeof(double2) * (n + 2));
+    dev_alloc((float2**)&d.m32, sizeof(float2) * (n + 4));
+    CK(cudaMemset(d.m64, 0, sizeof(double2) * (n + 2)));
+    CK(cudaMemset(d.m32, 0, sizeof(float2) * (n + 4)));
     if (n) {
         CK(cudaMemcpy(d.m64, h.mats.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
         std::vector<float2> f(n);
@@ -222,90 +572,224 @@ void upload_bsr(BsrHost& h, BsrDev& d)
 void free_bsr(BsrDev& d)
 {
     cudaFree(d.rowptr);
+    cudaFree(d.rout);
     cudaFree(d.col);
+    cudaFree(d.rin);
+    cudaFree(d.moff);
     cudaFree(d.m64);
     cudaFree(d.m32);
     d = BsrDev();
 }
 
-template <typename T>
-void launch_bsr(const BsrDev& b, const void* x, int ldx, void* y, int ldy, int accumulate, cudaStream_t s)
+// Cut every row's matrix (rout x J, the row's blocks side by side) into
+// column ranges of at most kChunkElems entries and kMaxChunkCols columns.  A
+// row with exactly one chunk is written by that chunk directly; the others
+// are listed for the reduction.  ldx: stride of the pass's input buffer.
+void build_group(Group& g, const std::vector<PassRef>& passes, const std::vector<const BsrHost*>& hs, const std::vector<int>& ldx,
+                 int accumulate)
 {
-    using C = typename V2<T>::t;
-    if (b.nrows == 0) return;
-    const C* m = (const C*)(sizeof(T) == 8 ? b.m64 : b.m32);
-    unsigned grid = (unsigned)((b.nrows + kRowsPerCta - 1) / kRowsPerCta);
-    bsr_apply_kernel<T><<<grid, 32 * kRowsPerCta, 0, s>>>(b.nrows, b.rowptr, b.col, m, b.Rout, b.Rin, (const C*)x, ldx, (C*)y,
-                                                           ldy, accumulate);
+    if (passes.size() > (size_t)kMaxPass) fail(DAFMM_EBADARG, "too many passes in one launch group");
+    g.passes = passes;
+    g.accumulate = accumulate;
+    std::vector<int4> recs, rows;
+    int pld = 0;
+    for (size_t p = 0; p < hs.size(); p++) {
+        const BsrHost& b = *hs[p];
+        std::vector<long> rbase(b.nrows, 0);
+        std::vector<int> cbase(b.nrows + 1, 0), xmap;
+        for (int r = 0; r < b.nrows; r++) {
+            const int ro = b.rout[r];
+            if (b.rowptr[r + 1] > b.rowptr[r]) rbase[r] = b.moff[b.rowptr[r]];
+            for (int e = b.rowptr[r]; e < b.rowptr[r + 1]; e++)
+                for (int k = 0; k < b.rin[e]; k++) xmap.push_back(b.col[e] * ldx[p] + k);
+            cbase[r + 1] = (int)xmap.size();
+            if (ro <= 0) continue;
+            if (ro > 128) fail(DAFMM_EBADARG, "rank above 128; set max_rank or loosen eps_nca");
+            pld = std::max(pld, ro);
+            const int J = cbase[r + 1] - cbase[r];
+            const int ldr = b.ld[r];
+            const int per = (int)std::max<long>(1, std::min<long>(kMaxChunkCols, kChunkElems / ldr));
+            const int c0 = (int)(recs.size() / 2);
+            for (int j = 0; j < J; j += per) {
+                const int j1 = std::min(J, j + per);
+                const long elem = rbase[r] + (long)j * ldr;
+                recs.push_back(make_int4((int)p | (ro << 16), r, j1 - j, cbase[r] + j));
+                recs.push_back(make_int4((int)(elem & 0xffffffffL), (int)(elem >> 32), (j1 - j) * ldr, c0));
+            }
+            const int c1 = (int)(recs.size() / 2);
+            if (c1 - c0 == 1)
+                recs[2 * c0].x |= 1 << 8;  // the row's only chunk writes the row
+            else if (!(accumulate && c1 == c0))
+                rows.push_back(make_int4((int)p, r, c0, c1));
+        }
+        long* drb = nullptr;
+        int* dcb = nullptr;
+        int* dxm = nullptr;
+        upload_vec(rbase, &drb);
+        upload_vec(cbase, &dcb);
+        upload_vec(xmap, &dxm);
+        g.rbase.push_back(drb);
+        g.cbase.push_back(dcb);
+        g.xmap.push_back(dxm);
+    }
+    g.nch = (int)(recs.size() / 2);
+    g.nrows = (int)rows.size();
+    g.Pld = std::max(pld, 1);
+    upload_vec(recs, &g.chunks);
+    upload_vec(rows, &g.rows);
 }
 
-// Event k of the current profiled call (k = 0..4), or nullptr.
-cudaEvent_t prof_event(OpsDev& d, int k)
+void free_group(Group& g)
 {
-    if (!d.profile) return nullptr;
+    cudaFree(g.chunks);
+    cudaFree(g.rows);
+    for (long* p : g.rbase) cudaFree(p);
+    for (int* p : g.cbase) cudaFree(p);
+    for (int* p : g.xmap) cudaFree(p);
+    g = Group();
+}
+
+// Coefficient buffers and chunk partials of one application.
+template <typename T>
+struct Bufs {
+    using C = typename V2<T>::t;
+    C* mp[64] = {};
+    C* lc[64] = {};
+    C* part = nullptr;
+};
+
+template <typename T>
+PassArgs<T> pass_args(const Tree& t, const OpsDev& d, const Bufs<T>& b, const typename V2<T>::t* vin, const Group& g, int p)
+{
+    using C = typename V2<T>::t;
+    const PassRef& pr = g.passes[p];
+    const int nu = pr.level;
+    const LevelDev& l = d.lv[nu];
+    const BsrDev& bs = pr.kind == 0 ? l.up : (pr.kind == 1 ? l.m2l : l.down);
+    PassArgs<T> a;
+    a.rout = bs.rout;
+    a.rbase = g.rbase[p];
+    a.cbase = g.cbase[p];
+    a.xmap = g.xmap[p];
+    a.mats = (const C*)(sizeof(T) == 8 ? bs.m64 : bs.m32);
+    if (pr.kind == 0) {
+        a.x = nu == t.L ? vin : b.mp[nu + 1];
+        a.y = b.mp[nu];
+        a.ldy = l.Ro;
+    } else if (pr.kind == 1) {
+        a.x = b.mp[nu];
+        a.y = b.lc[nu];
+        a.ldy = l.Ri;
+    } else {
+        a.x = b.lc[nu];
+        a.y = b.lc[nu + 1];
+        a.ldy = d.lv[nu + 1].Ri;
+    }
+    return a;
+}
+
+template <typename T>
+void launch_group(const Tree& t, const OpsDev& d, const Bufs<T>& b, const typename V2<T>::t* vin, const Group& g, cudaStream_t s)
+{
+    if (g.nch == 0 && g.nrows == 0) return;
+    GroupArgs<T> ga;
+    std::memset(&ga, 0, sizeof(ga));
+    for (size_t p = 0; p < g.passes.size(); p++) ga.p[p] = pass_args<T>(t, d, b, vin, g, (int)p);
+    int kpw = 1;
+    if (g.nch > 0) {
+        static int sms = 0, per_sm[2] = {0, 0};
+        if (!sms) {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        int& psm = per_sm[sizeof(T) == 8];
+        if (!psm) {
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&psm, stream_kernel<T>, 32 * kStreamWarps, StreamCfg<T>::kCta));
+            psm = std::max(psm, 1);
+        }
+        const int ctas = std::max(1, std::min((g.nch + kStreamWarps - 1) / kStreamWarps, sms * psm));
+        const int warps = ctas * kStreamWarps;
+        kpw = (g.nch + warps - 1) / warps;
+        stream_kernel<T><<<(unsigned)ctas, 32 * kStreamWarps, StreamCfg<T>::kCta, s>>>(g.nch, kpw, g.chunks, ga, b.part, g.Pld,
+                                                                                       g.accumulate, d.err);
+    }
+    if (g.nrows > 0)
+        reduce_kernel<T><<<(unsigned)((g.nrows + kWarpsPerCta - 1) / kWarpsPerCta), 32 * kWarpsPerCta, 0, s>>>(
+            g.nrows, kpw, g.rows, ga, b.part, g.Pld, g.accumulate);
+}
+
+// Events recorded while a graph is being captured (its five pass marks).
+thread_local cudaEvent_t* tl_capture_events = nullptr;
+
+// Record event k (0..4) of the current profiled call on the handle d.
+void mark(OpsDev* d, int k, cudaStream_t s)
+{
+    if (tl_capture_events) {
+        // an external record node (a plain record in capture only orders streams)
+        CK(cudaEventRecordWithFlags(tl_capture_events[k], s, cudaEventRecordExternal));
+        return;
+    }
+    if (!d || !d->profile) return;
     if (k == 0) {
-        if (d.ev_used + 5 > (size_t)5 * 65536) return nullptr;
-        while (d.events.size() < d.ev_used + 5) {
+        if (d->ev_used + 5 > (size_t)5 * 65536) return;
+        while (d->events.size() < d->ev_used + 5) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e));
-            d.events.push_back(e);
+            d->events.push_back(e);
         }
-        d.ev_used += 5;
+        d->ev_used += 5;
     }
-    if (d.ev_used < 5) return nullptr;
-    return d.events[d.ev_used - 5 + k];
+    if (d->ev_used < 5) return;
+    CK(cudaEventRecord(d->events[d->ev_used - 5 + k], s));
 }
 
-void mark(OpsDev& d, int k, cudaStream_t s, bool& live)
-{
-    if (k == 0) live = d.profile && d.ev_used + 5 <= (size_t)5 * 65536;
-    if (!live) return;
-    cudaEvent_t e = prof_event(d, k);
-    if (e) CK(cudaEventRecord(e, s));
-}
-
+// The whole application on the given buffers.  prof: handle whose events
+// record the passes (nullptr: none).
 template <typename T>
-void run(const Tree& t, OpsDev& d, const double* v, double* out, cudaStream_t s)
+void run(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, const double* v, double* out, cudaStream_t s, OpsDev* prof)
 {
     using C = typename V2<T>::t;
-    bool live = false;
-    mark(d, 0, s, live);
     const int L = t.L;
     const long N = t.N;
     const int nleaf = t.nb * t.nb;
+    mark(prof, 0, s);
     const C* vin;
     if (sizeof(T) == 4) {
-        to_c64_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, (const double2*)v, d.v32);
-        vin = (const C*)d.v32;
+        to_c64_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, (const double2*)v, v32);
+        vin = (const C*)v32;
     } else {
         vin = (const C*)v;
     }
-    auto MP = [&](int nu) { return sizeof(T) == 8 ? d.lv[nu].mp64 : d.lv[nu].mp32; };
-    auto LC = [&](int nu) { return sizeof(T) == 8 ? d.lv[nu].lc64 : d.lv[nu].lc32; };
     const bool far = t.top <= L;
     if (far) {
         // upward pass: P2M at the leaves, M2M (and directional M2M) above
-        launch_bsr<T>(d.lv[L].up, vin, 16, MP(L), d.lv[L].Ro, 0, s);
-        for (int nu = L - 1; nu >= t.top; nu--) launch_bsr<T>(d.lv[nu].up, MP(nu + 1), d.lv[nu + 1].Ro, MP(nu), d.lv[nu].Ro, 0, s);
+        for (int nu = L; nu >= t.top; nu--) launch_group<T>(t, d, b, vin, d.up[nu], s);
     }
-    mark(d, 1, s, live);
-    if (far) {
-        // transverse pass: M2L at every level
-        for (int nu = t.top; nu <= L; nu++) launch_bsr<T>(d.lv[nu].m2l, MP(nu), d.lv[nu].Ro, LC(nu), d.lv[nu].Ri, 0, s);
-    }
-    mark(d, 2, s, live);
+    mark(prof, 1, s);
+    if (far) launch_group<T>(t, d, b, vin, d.m2l, s);  // transverse pass, every level
+    mark(prof, 2, s);
     if (far) {
         // downward pass: (directional) L2L into the children's locals
-        for (int nu = t.top; nu < L; nu++) launch_bsr<T>(d.lv[nu].down, LC(nu), d.lv[nu].Ri, LC(nu + 1), d.lv[nu + 1].Ri, 1, s);
+        for (int nu = t.top; nu < L; nu++) launch_group<T>(t, d, b, vin, d.down[nu], s);
     }
-    mark(d, 3, s, live);
-    const C* nearp = (const C*)(sizeof(T) == 8 ? (void*)d.near64 : (void*)d.near32);
+    mark(prof, 3, s);
+    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
     const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
     leaf_apply_kernel<T><<<(unsigned)((nleaf + 7) / 8), 128, 0, s>>>(
-        nleaf, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr,
-        far ? d.lv[L].Ri : 0, far ? (const C*)LC(L) : nullptr, (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
+        nleaf, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
+        l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
+        (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
     CK(cudaGetLastError());
-    mark(d, 4, s, live);
+    mark(prof, 4, s);
+}
+
+size_t max_group_part(const OpsDev& d)
+{
+    size_t m = (size_t)d.m2l.nch * d.m2l.Pld;
+    for (const Group& g : d.up) m = std::max(m, (size_t)g.nch * g.Pld);
+    for (const Group& g : d.down) m = std::max(m, (size_t)g.nch * g.Pld);
+    return m;
 }
 
 }  // namespace
@@ -314,10 +798,24 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
 {
     const int L = t.L;
     d.lv.assign(L + 1, LevelDev());
+    d.up.assign(L + 1, Group());
+    d.down.assign(L + 1, Group());
     if (t.top <= L) {
+        if (L - t.top + 1 > kMaxPass) fail(DAFMM_EBADARG, "too many far-field levels");
+        std::vector<PassRef> m2l_passes;
+        std::vector<const BsrHost*> m2l_hosts;
+        std::vector<int> m2l_ldx;
         for (int nu = t.top; nu <= L; nu++) {
             d.lv[nu].Ri = h.lv[nu].Ri;
             d.lv[nu].Ro = h.lv[nu].Ro;
+            build_group(d.up[nu], {PassRef{nu, 0}}, {&h.lv[nu].up}, {nu == L ? 16 : h.lv[nu + 1].Ro}, 0);
+            if (nu < L) build_group(d.down[nu], {PassRef{nu, 2}}, {&h.lv[nu].down}, {h.lv[nu].Ri}, 1);
+            m2l_passes.push_back(PassRef{nu, 1});
+            m2l_hosts.push_back(&h.lv[nu].m2l);
+            m2l_ldx.push_back(h.lv[nu].Ro);
+        }
+        build_group(d.m2l, m2l_passes, m2l_hosts, m2l_ldx, 0);
+        for (int nu = t.top; nu <= L; nu++) {
             upload_bsr(h.lv[nu].up, d.lv[nu].up);
             upload_bsr(h.lv[nu].m2l, d.lv[nu].m2l);
             upload_bsr(h.lv[nu].down, d.lv[nu].down);
@@ -333,10 +831,8 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
                 n64[o * 256 + j * 16 + i] = make_double2(v.real(), v.imag());
                 n32[o * 256 + j * 16 + i] = make_float2((float)v.real(), (float)v.imag());
             }
-    dev_alloc(&d.near64, sizeof(double2) * 9 * 256);
-    dev_alloc(&d.near32, sizeof(float2) * 9 * 256);
-    CK(cudaMemcpy(d.near64, n64.data(), sizeof(double2) * 9 * 256, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.near32, n32.data(), sizeof(float2) * 9 * 256, cudaMemcpyHostToDevice));
+    upload_vec(n64, &d.near64);
+    upload_vec(n32, &d.near32);
     // near-neighbour table of the leaves
     const int nleaf = t.nb * t.nb;
     std::vector<int> nbr((size_t)nleaf * 9, -1);
@@ -349,8 +845,12 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
                 nbr[(size_t)b * 9 + (sy + 1) * 3 + (sx + 1)] = (int)morton_encode(x, y);
             }
     }
-    dev_alloc(&d.nbr, sizeof(int) * nbr.size());
-    CK(cudaMemcpy(d.nbr, nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice));
+    upload_vec(nbr, &d.nbr);
+    dev_alloc(&d.err, sizeof(int));
+    CK(cudaMemset(d.err, 0, sizeof(int)));
+    CK(cudaFuncSetAttribute(stream_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, StreamCfg<float>::kCta));
+    CK(cudaFuncSetAttribute(stream_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, StreamCfg<double>::kCta));
+    d.part_elems = max_group_part(d);
     ensure_scratch(t, d, 1);
 }
 
@@ -358,13 +858,13 @@ void ensure_scratch(const Tree& t, OpsDev& d, int nrhs)
 {
     if (nrhs <= d.nrhs_cap) return;
     const int L = t.L;
-    for (int nu = 0; nu <= L && t.top <= L; nu++) {
-        if (nu < t.top) continue;
+    for (int nu = t.top; nu <= L; nu++) {
         LevelDev& l = d.lv[nu];
         cudaFree(l.mp64);
         cudaFree(l.lc64);
         cudaFree(l.mp32);
         cudaFree(l.lc32);
+        l.mp64 = l.lc64 = l.mp32 = l.lc32 = nullptr;
         const size_t ns = (size_t)t.lv[nu].nslot() * nrhs;
         dev_alloc((double2**)&l.mp64, sizeof(double2) * ns * l.Ro);
         dev_alloc((double2**)&l.lc64, sizeof(double2) * ns * l.Ri);
@@ -376,8 +876,17 @@ void ensure_scratch(const Tree& t, OpsDev& d, int nrhs)
         CK(cudaMemset(l.lc32, 0, sizeof(float2) * ns * l.Ri));
     }
     cudaFree(d.v32);
+    d.v32 = nullptr;
     dev_alloc(&d.v32, sizeof(float2) * (size_t)t.N * nrhs);
+    cudaFree(d.part);
+    d.part = nullptr;
+    dev_alloc((double2**)&d.part, sizeof(double2) * std::max<size_t>(d.part_elems, 1) * nrhs);
     d.nrhs_cap = nrhs;
+    for (auto& G : d.gc) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.graph) cudaGraphDestroy(G.graph);
+        G = GraphCache();
+    }
 }
 
 void profile_enable(OpsDev& d, bool on)
@@ -406,6 +915,13 @@ void free_ops(OpsDev& d)
 {
     for (cudaEvent_t e : d.events) cudaEventDestroy(e);
     d.events.clear();
+    for (auto& G : d.gc) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.graph) cudaGraphDestroy(G.graph);
+    }
+    for (cudaEvent_t e : d.placeholder)
+        if (e) cudaEventDestroy(e);
+    if (d.cap_stream) cudaStreamDestroy(d.cap_stream);
     for (auto& l : d.lv) {
         free_bsr(l.up);
         free_bsr(l.m2l);
@@ -415,35 +931,185 @@ void free_ops(OpsDev& d)
         cudaFree(l.mp32);
         cudaFree(l.lc32);
     }
+    for (auto& g : d.up) free_group(g);
+    for (auto& g : d.down) free_group(g);
+    free_group(d.m2l);
     d.lv.clear();
     cudaFree(d.near64);
     cudaFree(d.near32);
     cudaFree(d.nbr);
     cudaFree(d.q);
     cudaFree(d.v32);
+    cudaFree(d.part);
+    cudaFree(d.err);
     d = OpsDev();
 }
+
+int sync_and_check(OpsDev& d, cudaStream_t stream)
+{
+    CK(cudaStreamSynchronize(stream));
+    if (!d.err) return DAFMM_OK;
+    int flag = 0;
+    CK(cudaMemcpy(&flag, d.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(d.err, 0, sizeof(int)));
+        return DAFMM_ETIMEOUT;
+    }
+    return DAFMM_OK;
+}
+
+int launches_per_call(const Tree& t, const OpsDev& d, int precision)
+{
+    int n = 1 + (precision == DAFMM_MIXED ? 1 : 0);  // leaf kernel, conversion
+    if (t.top > t.L) return n;
+    auto cnt = [](const Group& g) { return (g.nch ? 1 : 0) + (g.nrows ? 1 : 0); };
+    for (int nu = t.top; nu <= t.L; nu++) n += cnt(d.up[nu]);
+    for (int nu = t.top; nu < t.L; nu++) n += cnt(d.down[nu]);
+    return n + cnt(d.m2l);
+}
+
+namespace {
+
+// Take five fresh events from the handle's pool for one profiled call.
+cudaEvent_t* next_profile_events(OpsDev& d)
+{
+    if (!d.profile || d.ev_used + 5 > (size_t)5 * 65536) return nullptr;
+    while (d.events.size() < d.ev_used + 5) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        d.events.push_back(e);
+    }
+    d.ev_used += 5;
+    return &d.events[d.ev_used - 5];
+}
+
+void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream, bool prof);
+
+// Capture the application into d.gc[precision] (on the private stream).
+void capture(const Tree& t, OpsDev& d, const double* v, double* out, int precision)
+{
+    if (!d.cap_stream) CK(cudaStreamCreateWithFlags(&d.cap_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 5; k++)
+        if (!d.placeholder[k]) CK(cudaEventCreate(&d.placeholder[k]));
+    GraphCache& G = d.gc[precision];
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(d.cap_stream, cudaStreamCaptureModeThreadLocal));
+    tl_capture_events = d.placeholder;
+    try {
+        run_eager(t, d, v, out, precision, d.cap_stream, false);
+    } catch (...) {
+        tl_capture_events = nullptr;
+        cudaStreamEndCapture(d.cap_stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+    }
+    tl_capture_events = nullptr;
+    CK(cudaStreamEndCapture(d.cap_stream, &graph));
+    if (G.exec) {
+        // same topology, new pointers: update in place; the exec keeps the
+        // node identities of the graph it was instantiated from
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(G.exec, graph, &info) == cudaSuccess) {
+            CK(cudaGraphDestroy(graph));
+            G.v = v;
+            G.out = out;
+            return;
+        }
+        cudaGetLastError();
+        cudaGraphExecDestroy(G.exec);
+        cudaGraphDestroy(G.graph);
+        G = GraphCache();
+    }
+    cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(graph);
+        G = GraphCache();
+        fail(DAFMM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    G.graph = graph;
+    // locate the event-record nodes of the five marks
+    size_t n = 0;
+    CK(cudaGraphGetNodes(graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CK(cudaGraphGetNodes(graph, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        CK(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        for (int k = 0; k < 5; k++)
+            if (ev == d.placeholder[k]) G.ev_node[k] = nd;
+    }
+    G.v = v;
+    G.out = out;
+}
+
+}  // namespace
 
 void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream)
 {
     if (nrhs != 1) fail(DAFMM_EBADARG, "this build applies one right-hand side per call");
+    if (t.L >= 64) fail(DAFMM_EBADARG, "tree too deep");
+    cudaGetLastError();  // launch checks below must see only this call's errors
     ensure_scratch(t, d, nrhs);
-    if (precision == DAFMM_FP64)
-        run<double>(t, d, v, out, stream);
-    else
-        run<float>(t, d, v, out, stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        // the caller is capturing: put the kernels into the caller's graph
+        run_eager(t, d, v, out, precision, stream, false);
+        return;
+    }
+    GraphCache& G = d.gc[precision];
+    if (!G.exec || G.v != v || G.out != out) capture(t, d, v, out, precision);
+    if (d.profile) {
+        cudaEvent_t* ev = next_profile_events(d);
+        for (int k = 0; k < 5; k++) {
+            cudaEvent_t e = ev ? ev[k] : d.placeholder[k];
+            if (G.ev_node[k]) CK(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_node[k], e));
+        }
+    } else {
+        for (int k = 0; k < 5; k++)
+            if (G.ev_node[k]) CK(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_node[k], d.placeholder[k]));
+    }
+    CK(cudaGraphLaunch(G.exec, stream));
 }
+
+namespace {
+void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream, bool prof)
+{
+    if (precision == DAFMM_FP64) {
+        Bufs<double> b;
+        for (int nu = t.top; nu <= t.L; nu++) {
+            b.mp[nu] = (double2*)d.lv[nu].mp64;
+            b.lc[nu] = (double2*)d.lv[nu].lc64;
+        }
+        b.part = (double2*)d.part;
+        run<double>(t, d, b, d.v32, v, out, stream, prof ? &d : nullptr);
+    } else {
+        Bufs<float> b;
+        for (int nu = t.top; nu <= t.L; nu++) {
+            b.mp[nu] = (float2*)d.lv[nu].mp32;
+            b.lc[nu] = (float2*)d.lv[nu].lc32;
+        }
+        b.part = (float2*)d.part;
+        run<float>(t, d, b, d.v32, v, out, stream, prof ? &d : nullptr);
+    }
+}
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // Allocation-free application.  Some callers cannot let the library allocate
 // device memory at call time: processes whose device memory is owned by their
 // own pool (a cudaMalloc there can fail or fragment the pool), hot loops that
 // cannot afford cudaMalloc's implicit device synchronisation, and deployments
-// that must fix all memory before they start.  For them the coefficient
-// scratch of one single-RHS application lives in this fixed device array
-// instead of the handle's grow-on-demand buffers.  Every GPU that loads the
-// library holds the array until the process exits; all calls on a device
-// share it, so calls whose kernels overlap in time on that device race.
+// that must fix all memory before they start.  For them the scratch of one
+// single-RHS application (coefficients, chunk partials, the complex64 copy of
+// the input) lives in this fixed device array instead of the handle's
+// grow-on-demand buffers.  Every GPU that loads the library holds the array
+// until the process exits; all calls on a device share it, so calls whose
+// kernels overlap in time on that device race.
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -478,13 +1144,11 @@ void run_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, c
     using C = typename V2<T>::t;
     const int L = t.L;
     const long N = t.N;
-    const int nleaf = t.nb * t.nb;
     const bool far = t.top <= L;
-    void* mp[64] = {};
-    void* lc[64] = {};
     if (L >= 64) fail(DAFMM_EBADARG, "tree too deep for the allocation-free path");
-    // carve the scratch: complex64 copy of v (mixed), then per level multipoles and locals
+    // layout: complex64 copy of v (mixed), chunk partials, then per level multipoles and locals
     size_t need = sizeof(T) == 4 ? align256(sizeof(float2) * (size_t)N) : 0;
+    need += align256(sizeof(C) * std::max<size_t>(d.part_elems, 1));
     if (far)
         for (int nu = t.top; nu <= L; nu++)
             need += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ro) +
@@ -496,37 +1160,29 @@ void run_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, c
     // the array keeps the previous call's contents: start from zeros
     CK(cudaMemsetAsync(base, 0, need, s));
     size_t off = 0;
-    const C* vin = (const C*)v;
+    float2* v32 = nullptr;
     if (sizeof(T) == 4) {
-        float2* v32 = (float2*)(base + off);
+        v32 = (float2*)(base + off);
         off += align256(sizeof(float2) * (size_t)N);
-        to_c64_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, (const double2*)v, v32);
-        vin = (const C*)v32;
     }
-    if (far) {
+    Bufs<T> b;
+    b.part = (C*)(base + off);
+    off += align256(sizeof(C) * std::max<size_t>(d.part_elems, 1));
+    if (far)
         for (int nu = t.top; nu <= L; nu++) {
-            mp[nu] = base + off;
+            b.mp[nu] = (C*)(base + off);
             off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ro);
-            lc[nu] = base + off;
+            b.lc[nu] = (C*)(base + off);
             off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ri);
         }
-        launch_bsr<T>(d.lv[L].up, vin, 16, mp[L], d.lv[L].Ro, 0, s);
-        for (int nu = L - 1; nu >= t.top; nu--) launch_bsr<T>(d.lv[nu].up, mp[nu + 1], d.lv[nu + 1].Ro, mp[nu], d.lv[nu].Ro, 0, s);
-        for (int nu = t.top; nu <= L; nu++) launch_bsr<T>(d.lv[nu].m2l, mp[nu], d.lv[nu].Ro, lc[nu], d.lv[nu].Ri, 0, s);
-        for (int nu = t.top; nu < L; nu++) launch_bsr<T>(d.lv[nu].down, lc[nu], d.lv[nu].Ri, lc[nu + 1], d.lv[nu + 1].Ri, 1, s);
-    }
-    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
-    const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
-    leaf_apply_kernel<T><<<(unsigned)((nleaf + 7) / 8), 128, 0, s>>>(
-        nleaf, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr,
-        far ? d.lv[L].Ri : 0, far ? (const C*)lc[L] : nullptr, (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
-    CK(cudaGetLastError());
+    run<T>(t, d, b, v32, v, out, s, nullptr);
 }
 
 }  // namespace
 
 void apply_matvec_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream)
 {
+    cudaGetLastError();  // launch checks below must see only this call's errors
     if (precision == DAFMM_FP64)
         run_noalloc<double>(t, d, v, out, stream);
     else

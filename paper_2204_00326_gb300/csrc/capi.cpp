@@ -118,10 +118,6 @@ void fill_stats(const Tree& t, const OpsHost& h, dafmm_stats_t& st)
     st.cmacs_down = c_down;
     st.cmacs_leaf = c_leaf + (double)p2p;
     st.coef_bytes_per_rhs = vec;
-    const int nlev = t.top <= L ? L - t.top + 1 : 0;
-    const int far_launches = nlev ? 1 + (nlev - 1) + nlev + (nlev - 1) : 0;
-    st.launches_per_call_fp64 = far_launches + 1;
-    st.launches_per_call = far_launches + 2;
 }
 
 }  // namespace dafmm
@@ -219,6 +215,8 @@ int build_nca_operators(dafmm_tree* tree, const double* q_dev, void* stream, daf
         ops->stats.setup_seconds_table = t_tab;
         ops->stats.setup_seconds_nca = h.t_nca;
         upload_ops(t, h, ops->dev);
+        ops->stats.launches_per_call = launches_per_call(t, ops->dev, DAFMM_MIXED);
+        ops->stats.launches_per_call_fp64 = launches_per_call(t, ops->dev, DAFMM_FP64);
         double* q = nullptr;
         if (cudaMalloc(&q, sizeof(double) * t.N) != cudaSuccess) {
             cudaGetLastError();
@@ -256,6 +254,17 @@ int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v, double* out, int
         if (v == out) fail(DAFMM_EBADARG, "v and out must not overlap");
         apply_matvec_noalloc(ops->tree->t, ops->dev, v, out, precision, (cudaStream_t)stream);
     });
+}
+
+int dafmm_sync(dafmm_ops* ops, void* stream)
+{
+    int st = DAFMM_OK;
+    int r = guarded([&] {
+        if (!ops) fail(DAFMM_EBADARG, "NULL argument");
+        st = sync_and_check(ops->dev, (cudaStream_t)stream);
+        if (st == DAFMM_ETIMEOUT) fail(DAFMM_ETIMEOUT, "a device-side wait gave up (bulk copy did not arrive in time)");
+    });
+    return r;
 }
 
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats)

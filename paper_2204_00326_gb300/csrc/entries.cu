@@ -217,7 +217,10 @@ __global__ void near_table_kernel(int nb, double kb, double beta2, double2* tab)
 #define CK(x)                                                                                     \
     do {                                                                                          \
         cudaError_t e_ = (x);                                                                     \
-        if (e_ != cudaSuccess) fail(DAFMM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGetLastError(); /* do not leave the error for a later check */                    \
+            fail(DAFMM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));                   \
+        }                                                                                         \
     } while (0)
 
 }  // namespace
@@ -226,6 +229,7 @@ double build_entry_table(const Tree& t, EntryTable& out, void* stream_)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
     auto t0 = std::chrono::steady_clock::now();
+    cudaGetLastError();  // launch checks below must see only this call's errors
     const int p = t.p, nb = t.nb;
     // Q^+ in closed form: first-kind nodes make Q^T Q diagonal,
     // Q^+_{(a,b),(k1,k2)} = T_a(z_k1) T_b(z_k2) / (c_a c_b), c_0 = p, c_a = p/2.

@@ -70,19 +70,45 @@ void cheb_nodes(int p, double* z);
 // ------------------------------------------------------------ operators ----
 
 // Block-sparse operator: for each output row r, y[r] (+)= sum_e M_e x[col_e].
-// Blocks are Rout x Rin complex, stored column-major (output index fastest).
+// Block e is rout[r] x rin[e] complex at its realised ranks, stored
+// column-major (output index fastest) with column stride ld[r] = rout[r]
+// rounded up to even, at offset moff[e] of mats; a row's blocks follow each
+// other, so the row is one ld x (sum of rin) matrix starting at an even offset.
 struct BsrHost {
-    int nrows = 0, Rout = 0, Rin = 0;
+    int nrows = 0;
+    int Rout = 0, Rin = 0;  // largest rout / rin (strides of the coefficient buffers)
     std::vector<int> rowptr, col;
-    std::vector<cd> mats;  // nnz * Rin * Rout
+    std::vector<int> rout;  // per row
+    std::vector<int> ld;    // per row: column stride (rout rounded up to even)
+    std::vector<int> rin;   // per entry
+    std::vector<long> moff; // per entry, in complex elements
+    std::vector<cd> mats;
     long nnz() const { return (long)col.size(); }
+    // fill ld, moff and size mats from rowptr, rout and rin
+    void layout()
+    {
+        moff.assign(col.size(), 0);
+        ld.assign(nrows, 0);
+        long off = 0;
+        for (int r = 0; r < nrows; r++) {
+            ld[r] = rout[r] + (rout[r] & 1);
+            for (int e = rowptr[r]; e < rowptr[r + 1]; e++) {
+                moff[e] = off;
+                off += (long)ld[r] * rin[e];
+            }
+        }
+        mats.assign((size_t)off, cd(0));
+    }
 };
 
 struct BsrDev {
     int nrows = 0, Rout = 0, Rin = 0;
-    long nnz = 0;
-    int* rowptr = nullptr;
+    long nnz = 0, nelem = 0;
+    int* rout = nullptr;
     int* col = nullptr;
+    int* rin = nullptr;
+    long* moff = nullptr;
+    int* rowptr = nullptr;
     void* m64 = nullptr;  // double2 blocks
     void* m32 = nullptr;  // float2 blocks
 };

@@ -317,7 +317,7 @@ void build_nca(const Tree& t, const EntryTable& K, OpsHost& ops)
         lo.Ro = pad_rank(romax);
     }
 
-    // ---- assemble block-sparse operators with padded ranks ----
+    // ---- assemble block-sparse operators at the realised ranks ----
     for (int nu = t.top; nu <= L; nu++) {
         const Level& l = t.lv[nu];
         LevelOpsHost& lo = ops.lv[nu];
@@ -330,32 +330,39 @@ void build_nca(const Tree& t, const EntryTable& K, OpsHost& ops)
             b.nrows = l.nslot();
             b.Rout = lo.Ri;
             b.Rin = lo.Ro;
+            b.rout = lo.ri;
             b.rowptr.assign(b.nrows + 1, 0);
             for (int s = 0; s < l.nslot(); s++) b.rowptr[s + 1] = b.rowptr[s] + (l.active[s] ? l.il_ptr[s + 1] - l.il_ptr[s] : 0);
             b.col.resize(b.rowptr.back());
-            b.mats.assign((size_t)b.col.size() * b.Rout * b.Rin, cd(0));
-#pragma omp parallel for schedule(dynamic, 8)
+            b.rin.resize(b.rowptr.back());
             for (int s = 0; s < l.nslot(); s++) {
                 if (!l.active[s]) continue;
-                int e0 = b.rowptr[s];
                 for (int e = l.il_ptr[s]; e < l.il_ptr[s + 1]; e++) {
-                    int a = l.il_idx[e];
-                    long slot_e = e0 + (e - l.il_ptr[s]);
-                    b.col[slot_e] = a;
-                    cd* M = &b.mats[(size_t)slot_e * b.Rout * b.Rin];
-                    const auto& ti = S[s].t_in;
-                    const auto& so = S[a].s_out;
+                    long k = b.rowptr[s] + (e - l.il_ptr[s]);
+                    b.col[k] = l.il_idx[e];
+                    b.rin[k] = lo.ro[l.il_idx[e]];
+                }
+            }
+            b.layout();
+#pragma omp parallel for schedule(dynamic, 8)
+            for (int s = 0; s < l.nslot(); s++) {
+                const auto& ti = S[s].t_in;
+                const size_t ldr = b.ld[s];
+                for (int k = b.rowptr[s]; k < b.rowptr[s + 1]; k++) {
+                    cd* M = &b.mats[b.moff[k]];
+                    const auto& so = S[b.col[k]].s_out;
                     for (size_t jj = 0; jj < so.size(); jj++)
-                        for (size_t ii = 0; ii < ti.size(); ii++) M[jj * b.Rout + ii] = K(ti[ii], so[jj]);
+                        for (size_t ii = 0; ii < ti.size(); ii++) M[jj * ldr + ii] = K(ti[ii], so[jj]);
                 }
             }
         }
-        // UP (P2M at the leaves, M2M above): rows slots of nu
+        // UP (P2M at the leaves, M2M above): rows slots of nu, blocks T (ro x ro_child) / V* (ro x 16)
         {
             BsrHost& b = lo.up;
             b.nrows = l.nslot();
             b.Rout = lo.Ro;
             b.Rin = leaf ? 16 : ops.lv[nu + 1].Ro;
+            b.rout = lo.ro;
             b.rowptr.assign(b.nrows + 1, 0);
             std::vector<std::vector<int>> cols(b.nrows);
             for (int s = 0; s < l.nslot(); s++) {
@@ -368,7 +375,14 @@ void build_nca(const Tree& t, const EntryTable& K, OpsHost& ops)
             }
             for (int s = 0; s < b.nrows; s++) b.rowptr[s + 1] += b.rowptr[s];
             b.col.resize(b.rowptr.back());
-            b.mats.assign((size_t)b.col.size() * b.Rout * b.Rin, cd(0));
+            b.rin.resize(b.rowptr.back());
+            for (int s = 0; s < l.nslot(); s++)
+                for (size_t c = 0; c < cols[s].size(); c++) {
+                    long e = b.rowptr[s] + (long)c;
+                    b.col[e] = cols[s][c];
+                    b.rin[e] = leaf ? 16 : ops.lv[nu + 1].ro[cols[s][c]];
+                }
+            b.layout();
             for (int s = 0; s < l.nslot(); s++) {
                 if (!l.active[s]) continue;
                 const SlotNCA& me = S[s];
@@ -376,10 +390,9 @@ void build_nca(const Tree& t, const EntryTable& K, OpsHost& ops)
                 const int ncand = me.out_off.back();
                 for (size_t c = 0; c < cols[s].size(); c++) {
                     long e = b.rowptr[s] + (long)c;
-                    b.col[e] = cols[s][c];
-                    cd* M = &b.mats[(size_t)e * b.Rout * b.Rin];
+                    cd* M = &b.mats[b.moff[e]];
                     for (int j = me.out_off[c]; j < me.out_off[c + 1]; j++)
-                        for (int a = 0; a < ro; a++) M[(size_t)(j - me.out_off[c]) * b.Rout + a] = me.Y[(size_t)a * ncand + j];
+                        for (int a = 0; a < ro; a++) M[(size_t)(j - me.out_off[c]) * b.ld[s] + a] = me.Y[(size_t)a * ncand + j];
                 }
             }
         }
@@ -390,17 +403,22 @@ void build_nca(const Tree& t, const EntryTable& K, OpsHost& ops)
                 b.nrows = l.nslot();
                 b.Rout = 16;
                 b.Rin = lo.Ri;
+                b.rout.assign(b.nrows, 16);
                 b.rowptr.assign(b.nrows + 1, 0);
                 for (int s = 0; s < l.nslot(); s++) b.rowptr[s + 1] = b.rowptr[s] + (l.active[s] ? 1 : 0);
                 b.col.resize(b.rowptr.back());
-                b.mats.assign((size_t)b.col.size() * b.Rout * b.Rin, cd(0));
+                b.rin.resize(b.rowptr.back());
+                for (int s = 0; s < l.nslot(); s++)
+                    if (l.active[s]) {
+                        b.col[b.rowptr[s]] = s;
+                        b.rin[b.rowptr[s]] = lo.ri[s];
+                    }
+                b.layout();
                 for (int s = 0; s < l.nslot(); s++) {
                     if (!l.active[s]) continue;
-                    long e = b.rowptr[s];
-                    b.col[e] = s;
                     const SlotNCA& me = S[s];
                     const int ri = (int)me.t_in.size();
-                    cd* M = &b.mats[(size_t)e * b.Rout * b.Rin];
+                    cd* M = &b.mats[b.moff[b.rowptr[s]]];
                     for (int jj = 0; jj < ri; jj++)
                         for (int a = 0; a < 16; a++) M[(size_t)jj * 16 + a] = me.X[(size_t)a * ri + jj];
                 }
@@ -410,6 +428,7 @@ void build_nca(const Tree& t, const EntryTable& K, OpsHost& ops)
                 b.nrows = lc.nslot();
                 b.Rout = loc.Ri;
                 b.Rin = lo.Ri;
+                b.rout = loc.ri;
                 std::vector<std::vector<std::pair<int, int>>> ent(b.nrows);  // (parent slot, child position)
                 for (int s = 0; s < l.nslot(); s++) {
                     if (!l.active[s]) continue;
@@ -420,18 +439,24 @@ void build_nca(const Tree& t, const EntryTable& K, OpsHost& ops)
                 b.rowptr.assign(b.nrows + 1, 0);
                 for (int r = 0; r < b.nrows; r++) b.rowptr[r + 1] = b.rowptr[r] + (int)ent[r].size();
                 b.col.resize(b.rowptr.back());
-                b.mats.assign((size_t)b.col.size() * b.Rout * b.Rin, cd(0));
+                b.rin.resize(b.rowptr.back());
+                for (int r = 0; r < b.nrows; r++)
+                    for (size_t k = 0; k < ent[r].size(); k++) {
+                        b.col[b.rowptr[r] + k] = ent[r][k].first;
+                        b.rin[b.rowptr[r] + k] = lo.ri[ent[r][k].first];
+                    }
+                b.layout();
 #pragma omp parallel for schedule(dynamic, 16)
                 for (int r = 0; r < b.nrows; r++) {
+                    const int rc = b.ld[r];
                     for (size_t k = 0; k < ent[r].size(); k++) {
                         long e = b.rowptr[r] + (long)k;
                         int s = ent[r][k].first, c = ent[r][k].second;
-                        b.col[e] = s;
                         const SlotNCA& me = S[s];
                         const int ri = (int)me.t_in.size();
-                        cd* M = &b.mats[(size_t)e * b.Rout * b.Rin];
+                        cd* M = &b.mats[b.moff[e]];
                         for (int a = me.in_off[c]; a < me.in_off[c + 1]; a++)
-                            for (int jj = 0; jj < ri; jj++) M[(size_t)jj * b.Rout + (a - me.in_off[c])] = me.X[(size_t)a * ri + jj];
+                            for (int jj = 0; jj < ri; jj++) M[(size_t)jj * rc + (a - me.in_off[c])] = me.X[(size_t)a * ri + jj];
                     }
                 }
             }

@@ -11,8 +11,9 @@ struct dafmm_tree {
 
 namespace dafmm {
 
+// Operators of one level and its coefficient scratch.
 struct LevelDev {
-    int Ri = 0, Ro = 0;
+    int Ri = 0, Ro = 0;  // strides of the local / multipole buffers
     BsrDev up, m2l, down;
     // coefficient scratch, grown with nrhs: multipoles [slot][Ro][nrhs], locals [slot][Ri][nrhs]
     void* mp64 = nullptr;
@@ -21,18 +22,61 @@ struct LevelDev {
     void* lc32 = nullptr;
 };
 
+// Block-sparse passes launched together: their rows are cut into chunks of
+// at most a few thousand block entries, one warp per chunk; a second kernel
+// sums each row's chunk partials in a fixed order.
+struct PassRef {
+    int level = 0;
+    int kind = 0;  // 0 up (P2M/M2M), 1 M2L, 2 down (L2L)
+};
+
+struct Group {
+    std::vector<PassRef> passes;
+    int nch = 0;             // chunks
+    int nrows = 0;           // rows summed by the reduction
+    int Pld = 0;             // stride of a chunk's partial (largest row rank)
+    int4* chunks = nullptr;  // two int4 per chunk (a column range of a row's matrix), see apply.cu
+    int4* rows = nullptr;    // {pass, row, chunk0, chunk1}
+    int accumulate = 0;      // add into y instead of overwriting
+    // per pass: element offset of each row's matrix, offset of each row's
+    // columns in xmap, and for every column the index of its input coefficient
+    std::vector<long*> rbase;
+    std::vector<int*> cbase;
+    std::vector<int*> xmap;
+};
+
+// One captured application (per precision), replayed while the vector
+// pointers stay the same.
+struct GraphCache {
+    cudaGraph_t graph = nullptr;      // the graph exec was instantiated from (owns ev_node)
+    cudaGraphExec_t exec = nullptr;
+    const double* v = nullptr;
+    double* out = nullptr;
+    cudaGraphNode_t ev_node[5] = {};  // event-record nodes of the five pass marks
+};
+
 struct OpsDev {
     std::vector<LevelDev> lv;
+    std::vector<Group> up;      // per level (index = level)
+    Group m2l;                  // every level at once
+    std::vector<Group> down;    // per level (index = parent level)
     double2* near64 = nullptr;  // 9 x 16 x 16, source offset (sx,sy) -> (sy+1)*3+(sx+1)
     float2* near32 = nullptr;
     int* nbr = nullptr;         // [nleaf][9] source leaf of each near offset, -1 outside
     double* q = nullptr;        // contrast at the N nodes
     float2* v32 = nullptr;      // complex64 copy of the input (mixed precision)
+    void* part = nullptr;       // chunk partials of the largest group (complex128 size)
+    size_t part_elems = 0;      // complex elements per right-hand side in part
     int nrhs_cap = 0;           // scratch sized for this many right-hand sides
+    int* err = nullptr;         // device flag: a bounded wait in a kernel gave up
     // per-pass timing: 5 events per profiled call (start, up, m2l, down, leaf)
     bool profile = false;
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
+    // graph replay
+    cudaStream_t cap_stream = nullptr;   // private stream used only for capture
+    cudaEvent_t placeholder[5] = {};     // events recorded by freshly captured graphs
+    GraphCache gc[2];
 };
 
 // Allocate and upload; frees host block storage as it goes.
@@ -46,6 +90,10 @@ void ensure_scratch(const Tree& t, OpsDev& d, int nrhs);
 void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream);
 // Same operator, one right-hand side, scratch in a static device array.
 void apply_matvec_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream);
+// Kernels one application launches.
+int launches_per_call(const Tree& t, const OpsDev& d, int precision);
+// Synchronise the stream and report (and clear) a device-side wait timeout.
+int sync_and_check(OpsDev& d, cudaStream_t stream);
 
 }  // namespace dafmm
 

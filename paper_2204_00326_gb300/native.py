@@ -108,6 +108,7 @@ _sig = {
     "build_nca_operators": ([_P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "dafmm_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_stats": ([_P, ctypes.POINTER(dafmm_stats_t)], ctypes.c_int),
     "dafmm_entries": ([_P, ctypes.c_long, _P, ctypes.c_long, _P, _P], ctypes.c_int),
     "dafmm_profile": ([_P, ctypes.c_int], ctypes.c_int),
@@ -209,6 +210,11 @@ def dafmm_matvec_noalloc(ops: int, v, out, precision: int = DAFMM_FP64, stream=N
     if v.dim() != 1 or out.shape != v.shape:
         raise ValueError("one right-hand side: v and out are (N,) vectors")
     _check(lib.dafmm_matvec_noalloc(ops, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
+
+
+def dafmm_sync(ops: int, stream=None) -> None:
+    """Synchronise and raise DafmmError(DAFMM_ETIMEOUT) if a device wait gave up."""
+    _check(lib.dafmm_sync(ops, _stream_ptr(stream)))
 
 
 def dafmm_stats(ops: int) -> dafmm_stats_t:

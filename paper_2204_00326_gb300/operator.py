@@ -35,6 +35,9 @@ class DafmmOperator:
         N.dafmm_matvec(self.ops, v, out, precision, stream)
         return out
 
+    def sync(self, stream=None):
+        N.dafmm_sync(self.ops, stream)
+
     def stats(self):
         return N.dafmm_stats(self.ops)
 

@@ -131,6 +131,7 @@ def test_matvec_is_linear_and_repeatable(N, op128):
         tol = 1e-13 if prec == N.DAFMM_FP64 else 1e-5
         assert (torch.linalg.norm(yab - (ya + 2.5j * yb)) / torch.linalg.norm(yab)).item() < tol
         assert torch.equal(op128.matvec(a, precision=prec), ya)
+    op128.sync()  # no device-side wait gave up
 
 
 def test_matvec_argument_errors(N, op128):
@@ -152,3 +153,29 @@ def test_profile_records_passes(N, op128):
     N.dafmm_profile(op128.ops, False)
     assert p.calls == 3 and p.ms_m2l > 0 and p.ms_leaf > 0
     assert abs(p.ms_total - (p.ms_up + p.ms_m2l + p.ms_down + p.ms_leaf)) < 1e-6
+
+
+def test_graph_replay_follows_new_pointers(N, op128):
+    """The captured application is re-pointed when the caller's vectors change."""
+    vs = [torch.as_tensor(W.random_vector(op128.N, 1, seed=40 + k)[:, 0], device="cuda") for k in range(3)]
+    outs = [op128.matvec(v, precision=N.DAFMM_MIXED) for v in vs]
+    again = [op128.matvec(v, precision=N.DAFMM_MIXED) for v in reversed(vs)]
+    for o, a in zip(outs, reversed(again)):
+        assert torch.equal(o, a)
+    assert not torch.equal(outs[0], outs[1])
+    op128.sync()
+
+
+def test_capture_by_the_caller(N, op128):
+    """Inside the caller's own stream capture the kernels join the caller's graph."""
+    v = torch.as_tensor(W.random_vector(op128.N, 1, seed=50)[:, 0], device="cuda")
+    ref = op128.matvec(v, precision=N.DAFMM_FP64)
+    out = torch.empty_like(v)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        N.dafmm_matvec(op128.ops, v, out, N.DAFMM_FP64, s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)

@@ -116,6 +116,33 @@ typedef struct dafmm_profile_t {
 
 typedef struct dafmm_tree dafmm_tree;
 typedef struct dafmm_ops dafmm_ops;
+typedef struct dafmm_hodlr dafmm_hodlr;
+
+/* Options of gmres_solve. */
+typedef struct gmres_opts {
+    int restart;        /* Krylov dimension m of one cycle (1..128); 50 is typical */
+    int max_iters;      /* cap on inner iterations over all cycles */
+    double tol;         /* stop when |f - A x| / |f| <= tol (FP64 residual, Section 6) */
+    int precision;      /* DAFMM_FP64, or DAFMM_MIXED: inner cycles use complex64
+                           operators and each outer step refines in FP64 */
+    double inner_tol;   /* mixed precision: relative tolerance of one correction
+                           solve (1e-5 is typical) */
+    double* history;    /* optional host array: relative residuals (true residual at
+                           each restart, least-squares estimate in between) */
+    int history_len;    /* its length */
+    int reserved[6];    /* must be zero */
+} gmres_opts;
+
+/* What gmres_solve did. */
+typedef struct gmres_stats {
+    int iterations;        /* inner iterations (one operator application each) */
+    int outer_iterations;  /* true-residual checks after the first */
+    int matvecs;           /* dafmm_matvec calls, including the FP64 residuals */
+    int precond_applies;   /* hodlr_solve calls */
+    int converged;         /* 1 if the tolerance was met */
+    double rel_residual;   /* final |f - A x| / |f|, FP64 */
+    double seconds;        /* wall time of the call (it synchronises the stream) */
+} gmres_stats;
 
 /* Copy the message of the last failed call on this thread into buf (always
  * NUL-terminated when size > 0).  Returns the status code of that call. */
@@ -182,6 +209,65 @@ int build_nca_operators(dafmm_tree* tree, const double* q_dev, void* stream, daf
  * DAFMM_ENOMEM (growing scratch for a larger nrhs), DAFMM_ECUDA.
  */
 int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v_dev, double* out_dev, int precision, void* stream);
+
+/*
+ * gmres_solve -- solve A psi = f (Eq. 12a) with restarted flexible GMRES
+ * (Saad), right-preconditioned by the HODLR approximation M when M != NULL
+ * (the Hybrid solver, Eq. hybrid; right rather than left preconditioning so
+ * that GMRES minimises the unpreconditioned residual the paper's stopping
+ * rule measures).  Every outer step forms the true residual f - A x with the
+ * FP64 DAFMM; inner cycles apply A (and M) in opts->precision.  Arnoldi,
+ * Hessenberg, Givens rotations and vector updates are FP64 on the device.
+ * f_dev: N complex128 (not modified); x_dev: N complex128, in: initial guess,
+ * out: solution.  Allocates its Krylov workspace (N x (2m+1) complex128) for
+ * the duration of the call and synchronises the stream.
+ * Returns DAFMM_OK when converged, DAFMM_ENOTCONV when max_iters was reached
+ * (x holds the last iterate, st the residual), DAFMM_EBADARG, DAFMM_ENOMEM,
+ * DAFMM_ECUDA.
+ */
+int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, const double* f_dev, double* x_dev, const gmres_opts* opts, gmres_stats* st,
+                void* stream);
+
+/*
+ * hodlr_factor -- HODLR approximation A~ of A (Ambikasaran & Darve; the
+ * preconditioner of the paper's Hybrid solver, Section 6 and Eq. hybrid).
+ * The Morton-ordered index set is halved recursively down to leaves of
+ * leaf_size unknowns (a power of two, 32..1024; 64 is typical); at every node
+ * the two off-diagonal blocks of A are compressed by partially pivoted ACA,
+ * to the fixed rank `rank` (rank > 0, the paper's preconditioner with r = 5,
+ * 15, 25) or to relative accuracy tol (rank = 0).  The factorisation
+ * (recursive Sherman-Morrison-Woodbury, FP64 on the host; leaf blocks
+ * inverted by Gauss-Jordan with partial pivoting) is uploaded in complex128
+ * and complex64.  Uses the entries tabulated by build_nca_operators, so the
+ * ops handle must outlive nothing here: A~ is self-contained once built.
+ * Synchronous.  Errors: DAFMM_EBADARG, DAFMM_ENOMEM, DAFMM_EBREAKDOWN
+ * (singular leaf block or Woodbury system), DAFMM_ECUDA.
+ */
+int hodlr_factor(const dafmm_ops* ops, int rank, double tol, int leaf_size, dafmm_hodlr** out);
+
+/*
+ * hodlr_solve -- x = A~^{-1} b for one right-hand side (nrhs must be 1):
+ * batched leaf inverses, then per level from the leaves up t = W x, s =
+ * S^{-1} t, x -= Ut s.  Cost O(r N log N).  b_dev, x_dev: N complex128 on
+ * the device; x_dev == b_dev is allowed.  precision: DAFMM_FP64, or
+ * DAFMM_MIXED (complex64 factors and arithmetic, complex128 boundary
+ * vectors).  Asynchronous on stream.
+ */
+int hodlr_solve(const dafmm_hodlr* M, int nrhs, const double* b_dev, double* x_dev, int precision, void* stream);
+
+/*
+ * hodlr_export -- the dense N x N matrix A~ assembled from the factors
+ * (dense leaf blocks plus U V products off the diagonal), row-major complex
+ * interleaved, into dense_host (caller-owned, 16 N^2 bytes).  For checking
+ * hodlr_solve against a dense solve; meant for small N.
+ */
+int hodlr_export(const dafmm_hodlr* M, double* dense_host);
+
+/* Shape of a HODLR factorisation. */
+int hodlr_info(const dafmm_hodlr* M, long* N, int* levels, int* leaf_size, int* rank_max, double* factor_seconds);
+
+/* Release a HODLR factorisation.  NULL is accepted. */
+int hodlr_destroy(dafmm_hodlr* M);
 
 /* Size of the static device scratch used by dafmm_matvec_noalloc. */
 #define DAFMM_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -256,6 +256,75 @@ int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v, double* out, int
     });
 }
 
+int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, const double* f, double* x, const gmres_opts* opts, gmres_stats* st,
+                void* stream)
+{
+    int code = DAFMM_OK;
+    int r = guarded([&] {
+        if (!ops || !f || !x || !opts || !st) fail(DAFMM_EBADARG, "NULL argument");
+        if (opts->restart < 1 || opts->restart > 128) fail(DAFMM_EBADARG, "restart must lie in 1..128");
+        if (opts->max_iters < 0) fail(DAFMM_EBADARG, "max_iters must be >= 0");
+        if (!(opts->tol > 0)) fail(DAFMM_EBADARG, "tol must be positive");
+        if (opts->precision != DAFMM_FP64 && opts->precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+        if (opts->precision == DAFMM_MIXED && !(opts->inner_tol > 0 && opts->inner_tol < 1))
+            fail(DAFMM_EBADARG, "inner_tol must lie in (0, 1) in mixed precision");
+        for (int v : opts->reserved)
+            if (v) fail(DAFMM_EBADARG, "reserved options must be zero");
+        if (f == x) fail(DAFMM_EBADARG, "f and x must not overlap");
+        PrecFn prec = nullptr;
+        if (M) {
+            if (hodlr_tree(M) != ops->tree) fail(DAFMM_EBADARG, "the preconditioner was built on another tree");
+            prec = hodlr_prec;
+        }
+        code = gmres_run(ops->tree->t, ops->dev, M, prec, f, x, *opts, *st, (cudaStream_t)stream);
+        if (code == DAFMM_ENOTCONV)
+            fail(DAFMM_ENOTCONV, "GMRES reached max_iters at relative residual " + std::to_string(st->rel_residual));
+    });
+    return r;
+}
+
+int hodlr_factor(const dafmm_ops* ops, int rank, double tol, int leaf_size, dafmm_hodlr** out)
+{
+    return guarded([&] {
+        if (!ops || !out) fail(DAFMM_EBADARG, "NULL argument");
+        *out = nullptr;
+        require_device();
+        *out = hodlr_build(ops, rank, tol, leaf_size);
+    });
+}
+
+int hodlr_solve(const dafmm_hodlr* M, int nrhs, const double* b, double* x, int precision, void* stream)
+{
+    return guarded([&] {
+        if (!M || !b || !x) fail(DAFMM_EBADARG, "NULL argument");
+        if (nrhs != 1) fail(DAFMM_EBADARG, "hodlr_solve applies one right-hand side per call");
+        if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+        hodlr_apply(M, b, x, precision, (cudaStream_t)stream);
+    });
+}
+
+int hodlr_export(const dafmm_hodlr* M, double* dense)
+{
+    return guarded([&] {
+        if (!M || !dense) fail(DAFMM_EBADARG, "NULL argument");
+        hodlr_dense(M, (cd*)dense);
+    });
+}
+
+int hodlr_info(const dafmm_hodlr* M, long* N, int* levels, int* leaf_size, int* rank_max, double* seconds)
+{
+    return guarded([&] {
+        if (!M || !N || !levels || !leaf_size || !rank_max || !seconds) fail(DAFMM_EBADARG, "NULL argument");
+        hodlr_shape(M, N, levels, leaf_size, rank_max, seconds);
+    });
+}
+
+int hodlr_destroy(dafmm_hodlr* M)
+{
+    hodlr_free(M);
+    return DAFMM_OK;
+}
+
 int dafmm_sync(dafmm_ops* ops, void* stream)
 {
     int st = DAFMM_OK;

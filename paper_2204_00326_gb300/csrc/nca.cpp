@@ -7,98 +7,16 @@
 #include <cmath>
 #include <cstring>
 
+#include "aca.h"
 #include "internal.h"
 
 namespace dafmm {
 namespace {
 
-// Partially pivoted ACA on the implicit matrix K(R[a], C[b]) (Section 4.2.2).
-// Stops when |u_k| |v_k| <= eps |S_k|_F with the Frobenius norm of the
-// approximant updated recursively (Rjasanow); the pivot of that last update
-// is not kept.  Starts at the first row; the
-// next row is the unused row of largest |u_k|, the pivot column the unused
-// column of largest residual; ties go to the lowest index; a row whose
-// residual vanishes is skipped for the next unused row.
-struct AcaPivots {
-    std::vector<int> r, c;
-};
-
 AcaPivots aca(const EntryTable& K, const std::vector<long>& R, const std::vector<long>& C, double eps, int maxr)
 {
-    const int m = (int)R.size(), n = (int)C.size();
     AcaPivots out;
-    if (m == 0 || n == 0) return out;
-    int kmax = std::min(m, n);
-    if (maxr > 0) kmax = std::min(kmax, maxr);
-    std::vector<std::vector<cd>> U, V;
-    std::vector<char> rused(m, 0), cused(n, 0);
-    std::vector<cd> row(n), u(m);
-    double s2 = 0.0, scale = 0.0;
-    int i = 0;
-    while ((int)out.r.size() < kmax) {
-        for (int j = 0; j < n; j++) {
-            cd a = K(R[i], C[j]);
-            scale = std::max(scale, std::abs(a));
-            for (size_t q = 0; q < U.size(); q++) a -= U[q][i] * V[q][j];
-            row[j] = a;
-        }
-        rused[i] = 1;
-        int jb = -1;
-        double best = 0.0;
-        for (int j = 0; j < n; j++)
-            if (!cused[j] && std::abs(row[j]) > best) {
-                best = std::abs(row[j]);
-                jb = j;
-            }
-        if (jb < 0 || best <= 1e-15 * scale) {
-            int nx = -1;
-            for (int a = 0; a < m; a++)
-                if (!rused[a]) { nx = a; break; }
-            if (nx < 0) break;
-            i = nx;
-            continue;
-        }
-        const cd delta = row[jb];
-        std::vector<cd> v(n);
-        for (int j = 0; j < n; j++) v[j] = row[j] / delta;
-        for (int a = 0; a < m; a++) {
-            cd e = K(R[a], C[jb]);
-            for (size_t q = 0; q < U.size(); q++) e -= U[q][a] * V[q][jb];
-            u[a] = e;
-        }
-        cused[jb] = 1;
-        out.r.push_back(i);
-        out.c.push_back(jb);
-        double nu2 = 0, nv2 = 0;
-        for (int a = 0; a < m; a++) nu2 += std::norm(u[a]);
-        for (int j = 0; j < n; j++) nv2 += std::norm(v[j]);
-        for (size_t q = 0; q < U.size(); q++) {
-            cd uu = 0, vv = 0;
-            for (int a = 0; a < m; a++) uu += std::conj(U[q][a]) * u[a];
-            for (int j = 0; j < n; j++) vv += std::conj(V[q][j]) * v[j];
-            s2 += 2.0 * std::real(uu * vv);
-        }
-        s2 += nu2 * nv2;
-        U.push_back(u);
-        V.push_back(v);
-        if (std::sqrt(nu2 * nv2) <= eps * std::sqrt(std::max(s2, 0.0))) {
-            // the approximant before this update already meets the tolerance;
-            // keeping a pivot whose residual is at rounding level would make
-            // the skeleton's pivot block singular
-            out.r.pop_back();
-            out.c.pop_back();
-            break;
-        }
-        int nx = -1;
-        double bu = -1.0;
-        for (int a = 0; a < m; a++)
-            if (!rused[a] && std::abs(u[a]) > bu) {
-                bu = std::abs(u[a]);
-                nx = a;
-            }
-        if (nx < 0) break;
-        i = nx;
-    }
+    aca_run([&](long i, long j) { return K(i, j); }, R, C, eps, maxr, out, nullptr, nullptr);
     return out;
 }
 

@@ -90,6 +90,20 @@ void ensure_scratch(const Tree& t, OpsDev& d, int nrhs);
 void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream);
 // Same operator, one right-hand side, scratch in a static device array.
 void apply_matvec_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream);
+// GMRES (gmres.cu); prec: z = M^{-1} v, or nullptr.
+using PrecFn = void (*)(const void* M, const double* v, double* z, int precision, cudaStream_t s);
+int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double* f, double* x, const gmres_opts& o, gmres_stats& st,
+              cudaStream_t s);
+
+// HODLR (hodlr.cu)
+dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf);
+void hodlr_free(dafmm_hodlr* h);
+void hodlr_apply(const dafmm_hodlr* h, const double* b, double* x, int precision, cudaStream_t s);
+void hodlr_prec(const void* M, const double* v, double* z, int precision, cudaStream_t s);
+const dafmm_tree* hodlr_tree(const dafmm_hodlr* h);
+void hodlr_dense(const dafmm_hodlr* h, cd* out);
+void hodlr_shape(const dafmm_hodlr* h, long* N, int* levels, int* leaf, int* rank_max, double* seconds);
+
 // Kernels one application launches.
 int launches_per_call(const Tree& t, const OpsDev& d, int precision);
 // Synchronise the stream and report (and clear) a device-side wait timeout.

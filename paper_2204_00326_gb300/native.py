@@ -93,6 +93,31 @@ class dafmm_profile_t(ctypes.Structure):
     ]
 
 
+class gmres_opts(ctypes.Structure):
+    _fields_ = [
+        ("restart", ctypes.c_int),
+        ("max_iters", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("history", ctypes.POINTER(ctypes.c_double)),
+        ("history_len", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
+    ]
+
+
+class gmres_stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("outer_iterations", ctypes.c_int),
+        ("matvecs", ctypes.c_int),
+        ("precond_applies", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("rel_residual", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_2204_00326_gb300.build()")
 lib = ctypes.CDLL(LIB_PATH)
@@ -109,6 +134,13 @@ _sig = {
     "dafmm_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
+    "gmres_solve": ([_P, _P, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
+    "hodlr_factor": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "hodlr_solve": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "hodlr_export": ([_P, _P], ctypes.c_int),
+    "hodlr_info": ([_P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "hodlr_destroy": ([_P], ctypes.c_int),
     "dafmm_stats": ([_P, ctypes.POINTER(dafmm_stats_t)], ctypes.c_int),
     "dafmm_entries": ([_P, ctypes.c_long, _P, ctypes.c_long, _P, _P], ctypes.c_int),
     "dafmm_profile": ([_P, ctypes.c_int], ctypes.c_int),
@@ -239,6 +271,58 @@ def dafmm_profile_read(ops: int) -> dafmm_profile_t:
     p = dafmm_profile_t()
     _check(lib.dafmm_profile_read(ops, ctypes.byref(p)))
     return p
+
+
+def gmres_solve(ops: int, f, x, tol: float = 1e-8, precision: int = DAFMM_FP64, restart: int = 50, max_iters: int = 1000,
+                inner_tol: float = 1e-5, M: int | None = None, stream=None, history_len: int = 0):
+    """Solve A x = f (x holds the initial guess on entry).  Returns (status, stats, history).
+
+    status is DAFMM_OK or DAFMM_ENOTCONV (not converged within max_iters); other
+    failures raise DafmmError.
+    """
+    o = gmres_opts()
+    o.restart = restart
+    o.max_iters = max_iters
+    o.tol = tol
+    o.precision = precision
+    o.inner_tol = inner_tol
+    hist = None
+    if history_len > 0:
+        hist = (ctypes.c_double * history_len)()
+        o.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        o.history_len = history_len
+    st = gmres_stats()
+    rc = lib.gmres_solve(ops, M, _dptr(f, "complex128"), _dptr(x, "complex128"), ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
+    if rc not in (DAFMM_OK, DAFMM_ENOTCONV):
+        _check(rc)
+    h = list(hist)[: min(history_len, st.iterations + st.outer_iterations + 1)] if hist is not None else None
+    return rc, st, h
+
+
+def hodlr_factor(ops: int, rank: int = 15, tol: float = 0.0, leaf_size: int = 64) -> int:
+    h = _P()
+    _check(lib.hodlr_factor(ops, rank, tol, leaf_size, ctypes.byref(h)))
+    return h.value
+
+
+def hodlr_solve(M: int, b, x, precision: int = DAFMM_FP64, stream=None) -> None:
+    _check(lib.hodlr_solve(M, 1, _dptr(b, "complex128"), _dptr(x, "complex128"), precision, _stream_ptr(stream)))
+
+
+def hodlr_export(M: int, N: int) -> np.ndarray:
+    out = np.zeros((N, N, 2))
+    _check(lib.hodlr_export(M, out.ctypes.data))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def hodlr_info(M: int) -> dict:
+    N, lv, lf, rk, sec = ctypes.c_long(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib.hodlr_info(M, ctypes.byref(N), ctypes.byref(lv), ctypes.byref(lf), ctypes.byref(rk), ctypes.byref(sec)))
+    return {"N": N.value, "levels": lv.value, "leaf_size": lf.value, "rank_max": rk.value, "factor_seconds": sec.value}
+
+
+def hodlr_destroy(M: int) -> None:
+    _check(lib.hodlr_destroy(M))
 
 
 def ops_destroy(ops: int) -> None:

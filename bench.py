@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--workload", default=W.GRID128_K40.name, choices=sorted(W.WORKLOADS))
     ap.add_argument("--eps-nca", type=float, default=1e-12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-residual solves")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -309,6 +310,23 @@ def main():
               "frac": flops64 / (ms_m2l64 * 1e-3) / 1e9 / fp64_peak_gflops, "kernel": "stream_kernel<double>: M2L",
               "peak_kind": "nominal GB300 FP64 rate", "ms_per_launch": ms_m2l64}
 
+    # time to relative residual 1e-8 (FP64 residual), f = -kappa^2 q u_inc
+    ttr = None
+    if not a.no_solve:
+        f = torch.as_tensor(-w.kappa ** 2 * op.q * W.plane_waves(w.kappa, op.xy)[:, 0], device="cuda")
+        t0 = time.perf_counter()
+        M = N.hodlr_factor(op.ops, rank=15, leaf_size=64)
+        t_factor = time.perf_counter() - t0
+        ttr = {"tol": 1e-8, "rhs": "plane wave exp(i kappa x1)", "hodlr_factor_s": t_factor}
+        for name, prec, pre in (("fp64", N.DAFMM_FP64, None), ("mixed", N.DAFMM_MIXED, None),
+                                ("fp64_hodlr15", N.DAFMM_FP64, M), ("mixed_hodlr15", N.DAFMM_MIXED, M)):
+            for rep in range(2):  # the first solve warms up (graph capture, workspace)
+                x = torch.zeros_like(f)
+                rc, gs, _ = N.gmres_solve(op.ops, f, x, tol=1e-8, precision=prec, restart=50, max_iters=3000, M=pre)
+            ttr[name] = {"seconds": gs.seconds, "iterations": gs.iterations, "outer_iterations": gs.outer_iterations,
+                         "matvecs": gs.matvecs, "rel_residual": gs.rel_residual, "converged": bool(gs.converged)}
+        N.hodlr_destroy(M)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(w, a.cpu_seconds)
@@ -327,6 +345,7 @@ def main():
         "clocks": clk.summary(),
         "fp64": {"value": value64, "unit": "Munknowns/s", "ms_per_step": ms_fp64 / a.steps, "dtype": "c128", "roofline": roof64,
                  "gpu_launches": int(st.launches_per_call_fp64 * a.steps)},
+        "time_to_residual": ttr,
         "setup_s": {"total": setup_s, "entry_table": st.setup_seconds_table, "nca": st.setup_seconds_nca},
         "operator": {"bytes_fp32": st.operator_bytes_fp32, "bytes_fp64": st.operator_bytes_fp64,
                      "cmacs_per_rhs": st.cmacs_per_rhs},

@@ -882,11 +882,12 @@ void ensure_scratch(const Tree& t, OpsDev& d, int nrhs)
     d.part = nullptr;
     dev_alloc((double2**)&d.part, sizeof(double2) * std::max<size_t>(d.part_elems, 1) * nrhs);
     d.nrhs_cap = nrhs;
-    for (auto& G : d.gc) {
-        if (G.exec) cudaGraphExecDestroy(G.exec);
-        if (G.graph) cudaGraphDestroy(G.graph);
-        G = GraphCache();
-    }
+    for (auto& row : d.gc)
+        for (auto& G : row) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.graph) cudaGraphDestroy(G.graph);
+            G = GraphCache();
+        }
 }
 
 void profile_enable(OpsDev& d, bool on)
@@ -915,10 +916,11 @@ void free_ops(OpsDev& d)
 {
     for (cudaEvent_t e : d.events) cudaEventDestroy(e);
     d.events.clear();
-    for (auto& G : d.gc) {
-        if (G.exec) cudaGraphExecDestroy(G.exec);
-        if (G.graph) cudaGraphDestroy(G.graph);
-    }
+    for (auto& row : d.gc)
+        for (auto& G : row) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.graph) cudaGraphDestroy(G.graph);
+        }
     for (cudaEvent_t e : d.placeholder)
         if (e) cudaEventDestroy(e);
     if (d.cap_stream) cudaStreamDestroy(d.cap_stream);
@@ -985,13 +987,12 @@ cudaEvent_t* next_profile_events(OpsDev& d)
 
 void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream, bool prof);
 
-// Capture the application into d.gc[precision] (on the private stream).
-void capture(const Tree& t, OpsDev& d, const double* v, double* out, int precision)
+// Capture the application into the cache slot G (on the private stream).
+void capture(const Tree& t, OpsDev& d, const double* v, double* out, int precision, GraphCache& G)
 {
     if (!d.cap_stream) CK(cudaStreamCreateWithFlags(&d.cap_stream, cudaStreamNonBlocking));
     for (int k = 0; k < 5; k++)
         if (!d.placeholder[k]) CK(cudaEventCreate(&d.placeholder[k]));
-    GraphCache& G = d.gc[precision];
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(d.cap_stream, cudaStreamCaptureModeThreadLocal));
     tl_capture_events = d.placeholder;
@@ -1061,19 +1062,28 @@ void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* o
         run_eager(t, d, v, out, precision, stream, false);
         return;
     }
-    GraphCache& G = d.gc[precision];
-    if (!G.exec || G.v != v || G.out != out) capture(t, d, v, out, precision);
+    // a cached graph for these pointers, else the least recently used slot
+    GraphCache* G = nullptr;
+    for (auto& c : d.gc[precision])
+        if (c.exec && c.v == v && c.out == out) G = &c;
+    if (!G) {
+        G = &d.gc[precision][0];
+        for (auto& c : d.gc[precision])
+            if (c.used < G->used) G = &c;
+        capture(t, d, v, out, precision, *G);
+    }
+    G->used = ++d.gc_clock;
     if (d.profile) {
         cudaEvent_t* ev = next_profile_events(d);
         for (int k = 0; k < 5; k++) {
             cudaEvent_t e = ev ? ev[k] : d.placeholder[k];
-            if (G.ev_node[k]) CK(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_node[k], e));
+            if (G->ev_node[k]) CK(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_node[k], e));
         }
     } else {
         for (int k = 0; k < 5; k++)
-            if (G.ev_node[k]) CK(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_node[k], d.placeholder[k]));
+            if (G->ev_node[k]) CK(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_node[k], d.placeholder[k]));
     }
-    CK(cudaGraphLaunch(G.exec, stream));
+    CK(cudaGraphLaunch(G->exec, stream));
 }
 
 namespace {

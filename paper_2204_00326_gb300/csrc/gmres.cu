@@ -231,14 +231,14 @@ void dalloc(P** p, size_t bytes)
 struct Work {
     long N = 0;
     int m = 0, nrb = 0;
-    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t = nullptr;
+    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t = nullptr, *zin = nullptr;
     double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double2 *h1 = nullptr, *h2 = nullptr, *part = nullptr, *sc = nullptr;  // sc: scalars (norms^2)
     double* res = nullptr;
     double* res_host = nullptr;  // pinned
     ~Work()
     {
-        for (void* p : {(void*)V, (void*)Z, (void*)w, (void*)r, (void*)t, (void*)H, (void*)cs, (void*)sn, (void*)g, (void*)y, (void*)h1,
+        for (void* p : {(void*)V, (void*)Z, (void*)w, (void*)r, (void*)t, (void*)zin, (void*)H, (void*)cs, (void*)sn, (void*)g, (void*)y, (void*)h1,
                         (void*)h2, (void*)part, (void*)sc, (void*)res})
             cudaFree(p);
         if (res_host) cudaFreeHost(res_host);
@@ -271,6 +271,7 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
     dalloc(&W.w, sizeof(double2) * N);
     dalloc(&W.r, sizeof(double2) * N);
     dalloc(&W.t, sizeof(double2) * N);
+    dalloc(&W.zin, sizeof(double2) * N);
     dalloc(&W.H, sizeof(double2) * (m + 1) * m);
     dalloc(&W.cs, sizeof(double2) * m);
     dalloc(&W.sn, sizeof(double2) * m);
@@ -334,7 +335,9 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
             } else {
                 CK(cudaMemcpyAsync(zj, vj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
             }
-            apply_matvec(t, d, 1, (const double*)zj, (double*)W.w, o.precision, s);
+            // fixed buffers keep the captured application valid from one iteration to the next
+            CK(cudaMemcpyAsync(W.zin, zj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+            apply_matvec(t, d, 1, (const double*)W.zin, (double*)W.w, o.precision, s);
             st.matvecs++;
             // classical Gram-Schmidt, twice
             dots(W, W.V, N, j + 1, W.w, W.h1, 0, s);

@@ -53,7 +53,9 @@ struct GraphCache {
     const double* v = nullptr;
     double* out = nullptr;
     cudaGraphNode_t ev_node[5] = {};  // event-record nodes of the five pass marks
+    unsigned long long used = 0;      // last use (LRU replacement)
 };
+constexpr int kGraphSlots = 4;        // cached (v, out) pairs per precision
 
 struct OpsDev {
     std::vector<LevelDev> lv;
@@ -76,7 +78,8 @@ struct OpsDev {
     // graph replay
     cudaStream_t cap_stream = nullptr;   // private stream used only for capture
     cudaEvent_t placeholder[5] = {};     // events recorded by freshly captured graphs
-    GraphCache gc[2];
+    GraphCache gc[2][kGraphSlots];
+    unsigned long long gc_clock = 0;
 };
 
 // Allocate and upload; frees host block storage as it goes.

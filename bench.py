@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--eps-nca", type=float, default=1e-12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-residual solves")
+    ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides of the batched measurement (1 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -310,6 +311,31 @@ def main():
               "frac": flops64 / (ms_m2l64 * 1e-3) / 1e9 / fp64_peak_gflops, "kernel": "stream_kernel<double>: M2L",
               "peak_kind": "nominal GB300 FP64 rate", "ms_per_launch": ms_m2l64}
 
+    # several right-hand sides in one application: nrhs plane waves
+    batched = None
+    if a.nrhs > 1:
+        Vb = torch.as_tensor(W.plane_waves(w.kappa, op.xy, a.nrhs), device="cuda").contiguous()
+        Yb = torch.empty_like(Vb)
+        batched = {"nrhs": a.nrhs}
+        for name, prec in (("mixed", N.DAFMM_MIXED), ("fp64", N.DAFMM_FP64)):
+            for _ in range(a.warmup):
+                flush.zero_()
+                op.matvec(Vb, Yb, prec)
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+            for e0b, e1b in evs:
+                flush.zero_()
+                e0b.record(stream)
+                op.matvec(Vb, Yb, prec)
+                e1b.record(stream)
+            torch.cuda.synchronize()
+            msb = sum(x.elapsed_time(y) for x, y in evs) / a.steps
+            batched[name] = {"value": w.N * a.nrhs / (msb * 1e-3) / 1e6, "unit": "Munknowns/s (unknowns x rhs)",
+                             "ms_per_step": msb}
+        cm = st.cmacs_per_rhs * a.nrhs
+        batched["mixed"]["achieved_tflops"] = 8.0 * cm / (batched["mixed"]["ms_per_step"] * 1e-3) / 1e12
+        del Vb, Yb
+
     # time to relative residual 1e-8 (FP64 residual), f = -kappa^2 q u_inc
     ttr = None
     if not a.no_solve:
@@ -345,6 +371,7 @@ def main():
         "clocks": clk.summary(),
         "fp64": {"value": value64, "unit": "Munknowns/s", "ms_per_step": ms_fp64 / a.steps, "dtype": "c128", "roofline": roof64,
                  "gpu_launches": int(st.launches_per_call_fp64 * a.steps)},
+        "batched": batched,
         "time_to_residual": ttr,
         "setup_s": {"total": setup_s, "entry_table": st.setup_seconds_table, "nca": st.setup_seconds_nca},
         "operator": {"bytes_fp32": st.operator_bytes_fp32, "bytes_fp64": st.operator_bytes_fp64,

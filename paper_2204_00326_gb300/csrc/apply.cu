@@ -45,6 +45,7 @@ struct V2<float> {
 
 constexpr int kWarpsPerCta = 8;
 constexpr int kMaxPass = 12;        // passes in one launch group
+constexpr int kMaxRhs = 64;         // right-hand sides of one application
 constexpr long kChunkElems = 1024;  // matrix entries per chunk (8 KB in complex64)
 
 template <typename T>
@@ -427,6 +428,213 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(int nch, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Several right-hand sides (vectors [N][nrhs], coefficients [slot][R][nrhs]).
+// One CTA streams a chunk range through the same TMA pipeline; its warps
+// share each stage and split the right-hand sides (16 per warp).  Lane
+// (r, g) of a warp owns right-hand side r and the contiguous rows
+// [g h, g h + h) of the chunk's rows (h even, so rows come in 16-byte pairs
+// for complex64); per column it reads its rows' entries from shared memory
+// (broadcast across the 16 lanes of a half-warp) and the gathered input of
+// its right-hand side.  The operator is read once for all right-hand sides.
+constexpr int kRhsPerWarp = 16;
+constexpr int kMaxChunkColsB = kMaxChunkCols;  // gather buffer columns: every chunk record fits
+static_assert(kMaxChunkColsB >= kMaxChunkCols, "batched gather buffer smaller than a chunk");
+
+template <typename T>
+struct BatchCfg {
+    using C = typename V2<T>::t;
+    static constexpr int kStage = StreamCfg<T>::kStage;
+    __host__ __device__ static int xs_bytes(int nrhs_pad) { return kMaxChunkColsB * nrhs_pad * (int)sizeof(C); }
+    __host__ __device__ static int cta_bytes(int nrhs_pad) { return 2 * kStage + xs_bytes(nrhs_pad) + 128; }
+};
+
+template <typename T, int MR>
+__global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, int nrhs, int nrhs_pad, const int4* __restrict__ recs,
+                                                             const __grid_constant__ GroupArgs<T> g,
+                                                             typename V2<T>::t* __restrict__ P, int Pld, int accumulate,
+                                                             int* __restrict__ err)
+{
+    using C = typename V2<T>::t;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto stage = [&](int k) { return (C*)(smem + (size_t)k * BatchCfg<T>::kStage); };
+    C* xs = (C*)(smem + 2 * BatchCfg<T>::kStage);
+    unsigned long long* bar = (unsigned long long*)(smem + 2 * BatchCfg<T>::kStage + BatchCfg<T>::xs_bytes(nrhs_pad));
+    const int r = warp * kRhsPerWarp + (lane & 15);
+    const int gsel = lane >> 4;
+    const int cb = blockIdx.x * kpc;
+    const int ce = min(nch, cb + kpc);
+    if (cb >= ce) return;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int k = 0; k < 2 && cb + k < ce; k++) {
+            unsigned bytes;
+            const char* src = chunk_src<T>(g, recs[2 * (cb + k)], recs[2 * (cb + k) + 1], bytes);
+            tma_load(stage(k), src, bytes, &bar[k]);
+        }
+    }
+    __syncthreads();
+    T ar[MR], ai[MR];
+#pragma unroll
+    for (int m = 0; m < MR; m++) ar[m] = ai[m] = 0;
+    int pslot = cb;
+    for (int c = cb, it = 0; c < ce; c++, it++) {
+        const int s = it & 1;
+        const unsigned parity = (unsigned)((it >> 1) & 1);
+        const int4 ra = recs[2 * c];
+        const PassArgs<T>& pa = g.p[ra.x & 0xff];
+        const int ro = (ra.x >> 16) & 0xffff;
+        const int ld = ro + (ro & 1);
+        const int ncol = ra.z;
+        // gather this chunk's inputs for every right-hand side: xs[k][rr]
+        for (int q = tid; q < ncol * nrhs; q += blockDim.x) {
+            const int k = q / nrhs, rr = q - k * nrhs;
+            xs[k * nrhs_pad + rr] = pa.x[(size_t)pa.xmap[ra.w + k] * nrhs + rr];
+        }
+        const bool ok = __syncthreads_and(mbar_wait(&bar[s], parity));
+        if (!ok) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait(&bar[s], parity);
+                if (c + 1 < ce) mbar_wait(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+            }
+            __syncthreads();
+            return;
+        }
+        // rows of this lane: [gsel h, gsel h + h), h even
+        const int h = ((ro + 3) >> 2) << 1;
+        const int i0 = gsel * h;
+        const C* M = stage(s) + i0;
+        if (r < nrhs) {
+            for (int k = 0; k < ncol; k++) {
+                const C xv = xs[k * nrhs_pad + r];
+                const C* Mk = M + k * ld;
+#pragma unroll
+                for (int m = 0; m < MR; m += 2) {
+                    if (m < h && i0 + m < ro) {
+                        if constexpr (sizeof(T) == 4) {
+                            const float4 mm = *(const float4*)(Mk + m);
+                            ar[m] = fmaf(mm.x, xv.x, fmaf(-mm.y, xv.y, ar[m]));
+                            ai[m] = fmaf(mm.x, xv.y, fmaf(mm.y, xv.x, ai[m]));
+                            ar[m + 1] = fmaf(mm.z, xv.x, fmaf(-mm.w, xv.y, ar[m + 1]));
+                            ai[m + 1] = fmaf(mm.z, xv.y, fmaf(mm.w, xv.x, ai[m + 1]));
+                        } else {
+                            const C m0 = Mk[m], m1 = Mk[m + 1];
+                            ar[m] = fma(m0.x, xv.x, fma(-m0.y, xv.y, ar[m]));
+                            ai[m] = fma(m0.x, xv.y, fma(m0.y, xv.x, ai[m]));
+                            ar[m + 1] = fma(m1.x, xv.x, fma(-m1.y, xv.y, ar[m + 1]));
+                            ai[m + 1] = fma(m1.x, xv.y, fma(m1.y, xv.x, ai[m + 1]));
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();  // everyone is done with this stage and the gather buffer
+        if (tid == 0 && c + 2 < ce) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            unsigned nbytes;
+            const char* src = chunk_src<T>(g, recs[2 * (c + 2)], recs[2 * (c + 2) + 1], nbytes);
+            tma_load(stage(s), src, nbytes, &bar[s]);
+        }
+        const bool row_ends = (c + 1 == ce) || recs[2 * (c + 1)].x != ra.x || recs[2 * (c + 1)].y != ra.y;
+        if (row_ends) {
+            const bool direct = (ra.x >> 8) & 1;
+            if (r < nrhs) {
+                C* dst = direct ? pa.y + (size_t)ra.y * pa.ldy * nrhs : P + (size_t)pslot * Pld * nrhs;
+#pragma unroll
+                for (int m = 0; m < MR; m++) {
+                    const int i = i0 + m;
+                    if (i < ro && m < h) {
+                        C* q = dst + (size_t)i * nrhs + r;
+                        T re = ar[m], im = ai[m];
+                        if (direct && accumulate) {
+                            const C o = *q;
+                            re += o.x;
+                            im += o.y;
+                        }
+                        C o;
+                        o.x = re;
+                        o.y = im;
+                        *q = o;
+                    }
+                    ar[m] = ai[m] = 0;
+                }
+            }
+            pslot = c + 1;
+        }
+    }
+}
+
+// Batched reduction: one CTA per row, threads over (i, rhs).
+template <typename T>
+__global__ void reduce_batched_kernel(int nrows, int kpc, int nrhs, const int4* __restrict__ rows, const __grid_constant__ GroupArgs<T> g,
+                                      const typename V2<T>::t* __restrict__ P, int Pld, int accumulate)
+{
+    using C = typename V2<T>::t;
+    const int4 rw = rows[blockIdx.x];
+    const PassArgs<T>& pa = g.p[rw.x & 0xff];
+    const int ro = pa.rout[rw.y];
+    C* y = pa.y + (size_t)rw.y * pa.ldy * nrhs;
+    for (int q = threadIdx.x; q < ro * nrhs; q += blockDim.x) {
+        T sr = 0, si = 0;
+        if (accumulate) {
+            const C o = y[q];
+            sr = o.x;
+            si = o.y;
+        }
+        for (int c = rw.z; c < rw.w; c = (c / kpc + 1) * kpc) {
+            const C p = P[(size_t)c * Pld * nrhs + q];
+            sr += p.x;
+            si += p.y;
+        }
+        C o;
+        o.x = sr;
+        o.y = si;
+        y[q] = o;
+    }
+}
+
+// Batched leaf kernel: one CTA per leaf, threads over (node i, rhs r), rhs fastest.
+template <typename T>
+__global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__ nbr, const typename V2<T>::t* __restrict__ near,
+                                    const typename V2<T>::t* __restrict__ vin, const int* __restrict__ l2p_rowptr,
+                                    const long* __restrict__ l2p_moff, const int* __restrict__ l2p_rin,
+                                    const typename V2<T>::t* __restrict__ l2p, int ldl, const typename V2<T>::t* __restrict__ lc,
+                                    const double2* __restrict__ v, const double* __restrict__ q, double k2, double2* __restrict__ out)
+{
+    using C = typename V2<T>::t;
+    __shared__ C sn[9 * 256];
+    for (int k = threadIdx.x; k < 9 * 256; k += blockDim.x) sn[k] = near[k];
+    __syncthreads();
+    const int leaf = blockIdx.x;
+    for (int t = threadIdx.x; t < 16 * nrhs; t += blockDim.x) {
+        const int i = t / nrhs, r = t - i * nrhs;
+        T ar = 0, ai = 0;
+        for (int o = 0; o < 9; o++) {
+            const int src = nbr[leaf * 9 + o];
+            if (src < 0) continue;
+            const C* vs = vin + (size_t)src * 16 * nrhs + r;
+            const C* B = sn + o * 256 + i;
+#pragma unroll
+            for (int j = 0; j < 16; j++) cmac<T>(ar, ai, B[j * 16], vs[(size_t)j * nrhs]);
+        }
+        if (l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {
+            const int e = l2p_rowptr[leaf];
+            const C* U = l2p + l2p_moff[e] + i;
+            const C* u = lc + (size_t)leaf * ldl * nrhs + r;
+            const int ri = l2p_rin[e];
+            for (int j = 0; j < ri; j++) cmac<T>(ar, ai, U[j * 16], u[(size_t)j * nrhs]);
+        }
+        const size_t gi = ((size_t)leaf * 16 + i) * nrhs + r;
+        const double2 vv = v[gi];
+        const double sc = k2 * q[(size_t)leaf * 16 + i];
+        out[gi] = make_double2(vv.x + sc * (double)ar, vv.y + sc * (double)ai);
+    }
+}
+
 // One warp per row {pass, row, c0, c1}: y[row] (+)= the row's partials, in
 // chunk order.  Partials sit at the row's first chunk c0 and at every chunk
 // k * kpw (the first chunk of a warp's range) inside (c0, c1).
@@ -784,6 +992,91 @@ void run(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, const do
     mark(prof, 4, s);
 }
 
+template <typename T, int MR>
+void launch_batched_mr(const OpsDev& d, const Group& g, const GroupArgs<T>& ga, typename V2<T>::t* part, int nrhs, cudaStream_t s)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int nrhs_pad = (nrhs + kRhsPerWarp - 1) / kRhsPerWarp * kRhsPerWarp;
+    const int threads = 32 * (nrhs_pad / kRhsPerWarp);
+    const int smem = BatchCfg<T>::cta_bytes(nrhs_pad);
+    CK(cudaFuncSetAttribute(stream_batched_kernel<T, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_batched_kernel<T, MR>, threads, smem));
+    per_sm = std::max(per_sm, 1);
+    int kpc = 1;
+    if (g.nch > 0) {
+        const int ctas = std::max(1, std::min(g.nch, sms * per_sm));
+        kpc = (g.nch + ctas - 1) / ctas;
+        const int grid = (g.nch + kpc - 1) / kpc;
+        stream_batched_kernel<T, MR><<<(unsigned)grid, threads, smem, s>>>(g.nch, kpc, nrhs, nrhs_pad, g.chunks, ga, part, g.Pld,
+                                                                         g.accumulate, d.err);
+    }
+    if (g.nrows > 0)
+        reduce_batched_kernel<T><<<(unsigned)g.nrows, 256, 0, s>>>(g.nrows, kpc, nrhs, g.rows, ga, part, g.Pld, g.accumulate);
+}
+
+template <typename T>
+void launch_group_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, const typename V2<T>::t* vin, const Group& g, int nrhs,
+                          cudaStream_t s)
+{
+    if (g.nch == 0 && g.nrows == 0) return;
+    GroupArgs<T> ga;
+    std::memset(&ga, 0, sizeof(ga));
+    for (size_t p = 0; p < g.passes.size(); p++) ga.p[p] = pass_args<T>(t, d, b, vin, g, (int)p);
+    const int h = ((g.Pld + 3) >> 2) << 1;  // rows per lane of the widest row
+    if (h <= 8)
+        launch_batched_mr<T, 8>(d, g, ga, b.part, nrhs, s);
+    else if (h <= 16)
+        launch_batched_mr<T, 16>(d, g, ga, b.part, nrhs, s);
+    else if (h <= 24)
+        launch_batched_mr<T, 24>(d, g, ga, b.part, nrhs, s);
+    else if (h <= 32)
+        launch_batched_mr<T, 32>(d, g, ga, b.part, nrhs, s);
+    else
+        fail(DAFMM_EBADARG, "ranks above 64 are not supported with several right-hand sides");
+}
+
+template <typename T>
+void run_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, const double* v, double* out, int nrhs, cudaStream_t s,
+                 OpsDev* prof)
+{
+    using C = typename V2<T>::t;
+    const int L = t.L;
+    const long N = t.N;
+    const int nleaf = t.nb * t.nb;
+    mark(prof, 0, s);
+    const C* vin;
+    if (sizeof(T) == 4) {
+        const long n = N * nrhs;
+        to_c64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (const double2*)v, v32);
+        vin = (const C*)v32;
+    } else {
+        vin = (const C*)v;
+    }
+    const bool far = t.top <= L;
+    if (far)
+        for (int nu = L; nu >= t.top; nu--) launch_group_batched<T>(t, d, b, vin, d.up[nu], nrhs, s);
+    mark(prof, 1, s);
+    if (far) launch_group_batched<T>(t, d, b, vin, d.m2l, nrhs, s);
+    mark(prof, 2, s);
+    if (far)
+        for (int nu = t.top; nu < L; nu++) launch_group_batched<T>(t, d, b, vin, d.down[nu], nrhs, s);
+    mark(prof, 3, s);
+    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
+    const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
+    leaf_batched_kernel<T><<<(unsigned)nleaf, 256, 0, s>>>(
+        nleaf, nrhs, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
+        l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
+        (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
+    CK(cudaGetLastError());
+    mark(prof, 4, s);
+}
+
 size_t max_group_part(const OpsDev& d)
 {
     size_t m = (size_t)d.m2l.nch * d.m2l.Pld;
@@ -985,10 +1278,10 @@ cudaEvent_t* next_profile_events(OpsDev& d)
     return &d.events[d.ev_used - 5];
 }
 
-void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream, bool prof);
+void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, int precision, cudaStream_t stream, bool prof);
 
 // Capture the application into the cache slot G (on the private stream).
-void capture(const Tree& t, OpsDev& d, const double* v, double* out, int precision, GraphCache& G)
+void capture(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, int precision, GraphCache& G)
 {
     if (!d.cap_stream) CK(cudaStreamCreateWithFlags(&d.cap_stream, cudaStreamNonBlocking));
     for (int k = 0; k < 5; k++)
@@ -997,7 +1290,7 @@ void capture(const Tree& t, OpsDev& d, const double* v, double* out, int precisi
     CK(cudaStreamBeginCapture(d.cap_stream, cudaStreamCaptureModeThreadLocal));
     tl_capture_events = d.placeholder;
     try {
-        run_eager(t, d, v, out, precision, d.cap_stream, false);
+        run_eager(t, d, v, out, nrhs, precision, d.cap_stream, false);
     } catch (...) {
         tl_capture_events = nullptr;
         cudaStreamEndCapture(d.cap_stream, &graph);
@@ -1014,6 +1307,7 @@ void capture(const Tree& t, OpsDev& d, const double* v, double* out, int precisi
             CK(cudaGraphDestroy(graph));
             G.v = v;
             G.out = out;
+            G.nrhs = nrhs;
             return;
         }
         cudaGetLastError();
@@ -1045,13 +1339,14 @@ void capture(const Tree& t, OpsDev& d, const double* v, double* out, int precisi
     }
     G.v = v;
     G.out = out;
+    G.nrhs = nrhs;
 }
 
 }  // namespace
 
 void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream)
 {
-    if (nrhs != 1) fail(DAFMM_EBADARG, "this build applies one right-hand side per call");
+    if (nrhs < 1 || nrhs > kMaxRhs) fail(DAFMM_EBADARG, "nrhs must lie in 1..64");
     if (t.L >= 64) fail(DAFMM_EBADARG, "tree too deep");
     cudaGetLastError();  // launch checks below must see only this call's errors
     ensure_scratch(t, d, nrhs);
@@ -1059,18 +1354,18 @@ void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* o
     CK(cudaStreamIsCapturing(stream, &cs));
     if (cs != cudaStreamCaptureStatusNone) {
         // the caller is capturing: put the kernels into the caller's graph
-        run_eager(t, d, v, out, precision, stream, false);
+        run_eager(t, d, v, out, nrhs, precision, stream, false);
         return;
     }
     // a cached graph for these pointers, else the least recently used slot
     GraphCache* G = nullptr;
     for (auto& c : d.gc[precision])
-        if (c.exec && c.v == v && c.out == out) G = &c;
+        if (c.exec && c.v == v && c.out == out && c.nrhs == nrhs) G = &c;
     if (!G) {
         G = &d.gc[precision][0];
         for (auto& c : d.gc[precision])
             if (c.used < G->used) G = &c;
-        capture(t, d, v, out, precision, *G);
+        capture(t, d, v, out, nrhs, precision, *G);
     }
     G->used = ++d.gc_clock;
     if (d.profile) {
@@ -1087,7 +1382,7 @@ void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* o
 }
 
 namespace {
-void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream, bool prof)
+void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, int precision, cudaStream_t stream, bool prof)
 {
     if (precision == DAFMM_FP64) {
         Bufs<double> b;
@@ -1096,7 +1391,10 @@ void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int preci
             b.lc[nu] = (double2*)d.lv[nu].lc64;
         }
         b.part = (double2*)d.part;
-        run<double>(t, d, b, d.v32, v, out, stream, prof ? &d : nullptr);
+        if (nrhs == 1)
+            run<double>(t, d, b, d.v32, v, out, stream, prof ? &d : nullptr);
+        else
+            run_batched<double>(t, d, b, d.v32, v, out, nrhs, stream, prof ? &d : nullptr);
     } else {
         Bufs<float> b;
         for (int nu = t.top; nu <= t.L; nu++) {
@@ -1104,7 +1402,10 @@ void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int preci
             b.lc[nu] = (float2*)d.lv[nu].lc32;
         }
         b.part = (float2*)d.part;
-        run<float>(t, d, b, d.v32, v, out, stream, prof ? &d : nullptr);
+        if (nrhs == 1)
+            run<float>(t, d, b, d.v32, v, out, stream, prof ? &d : nullptr);
+        else
+            run_batched<float>(t, d, b, d.v32, v, out, nrhs, stream, prof ? &d : nullptr);
     }
 }
 }  // namespace

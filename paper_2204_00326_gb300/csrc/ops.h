@@ -52,6 +52,7 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     const double* v = nullptr;
     double* out = nullptr;
+    int nrhs = 0;
     cudaGraphNode_t ev_node[5] = {};  // event-record nodes of the five pass marks
     unsigned long long used = 0;      // last use (LRU replacement)
 };

@@ -179,3 +179,33 @@ def test_capture_by_the_caller(N, op128):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("nrhs", [2, 16, 37, 64])
+def test_batched_matvec_matches_single(N, op128, nrhs):
+    """Several right-hand sides in one application equal one-at-a-time applications."""
+    w = W.GRID128_K40
+    V = torch.as_tensor(W.random_vector(w.N, nrhs, seed=60 + nrhs), device="cuda").contiguous()
+    # FP32 sums grouped differently in the two paths: compare at the mixed tolerance
+    for prec, tol in ((N.DAFMM_FP64, 1e-13), (N.DAFMM_MIXED, MIXED_TOL)):
+        Y = op128.matvec(V, precision=prec)
+        for k in sorted({0, nrhs // 2, nrhs - 1}):
+            yk = op128.matvec(V[:, k].contiguous(), precision=prec)
+            assert (torch.linalg.norm(Y[:, k] - yk) / torch.linalg.norm(yk)).item() < tol
+    op128.sync()
+
+
+def test_batched_matvec_against_oracle_rows(N, op128):
+    w = W.GRID128_K40
+    nrhs = 8
+    V = W.plane_waves(w.kappa, op128.xy, nrhs) * (-w.kappa ** 2 * op128.q)[:, None]
+    Y = op128.matvec(torch.as_tensor(V, device="cuda").contiguous(), precision=N.DAFMM_FP64).cpu().numpy()
+    rows = np.sort(np.random.default_rng(13).choice(w.N, 32, replace=False))
+    ref = O.matvec_rows(w.n_side, w.kappa, op128.q, V, rows)
+    assert _rel(Y[rows], ref) < FP64_TOL
+
+
+def test_batched_rejects_too_many_rhs(N, op128):
+    V = torch.zeros(op128.N, 65, dtype=torch.complex128, device="cuda")
+    with pytest.raises(N.DafmmError):
+        op128.matvec(V)

@@ -31,6 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2204_00326_gb300 import replicas  # noqa: E402
 from paper_2204_00326_gb300 import workloads as W  # noqa: E402
 
 METRIC = "DAFMM matvec Munknowns/s; time-to-1e-8 residual, mixed vs FP64 on GB300"
@@ -251,14 +252,10 @@ def main():
         if profile:
             prof = N.dafmm_profile_read(op.ops)
             N.dafmm_profile(op.ops, False)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = t.item()
-        return ms, prof
+        return replicas.max_over_ranks(ms, device="cuda"), prof
 
-    with ClockSampler(local) as clk:
-        ms_mixed, prof_mixed = timed(N.DAFMM_MIXED, a.steps, True)
+    clk = ClockSampler(local).__enter__()
+    ms_mixed, prof_mixed = timed(N.DAFMM_MIXED, a.steps, True)
     ms_fp64, prof_fp64 = timed(N.DAFMM_FP64, a.steps, True)
 
     # end to end: pinned host input -> device -> matvec -> pinned host output
@@ -280,16 +277,11 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = t.item()
+    ms_e2e = replicas.max_over_ranks(e0.elapsed_time(e1), device="cuda")
 
-    units = float(w.N) * world * a.steps
-    value = units / (ms_mixed * 1e-3) / 1e6
-    value64 = units / (ms_fp64 * 1e-3) / 1e6
-    e2e = units / (ms_e2e * 1e-3) / 1e6
+    value = replicas.job_throughput(float(w.N) * a.steps, world, ms_mixed)
+    value64 = replicas.job_throughput(float(w.N) * a.steps, world, ms_fp64)
+    e2e = replicas.job_throughput(float(w.N) * a.steps, world, ms_e2e)
 
     hbm, peak_kind = _peaks()
     # dominant pass: the M2L of every level (stream_kernel launch + its reduction)
@@ -352,6 +344,8 @@ def main():
             ttr[name] = {"seconds": gs.seconds, "iterations": gs.iterations, "outer_iterations": gs.outer_iterations,
                          "matvecs": gs.matvecs, "rel_residual": gs.rel_residual, "converged": bool(gs.converged)}
         N.hodlr_destroy(M)
+
+    clk.__exit__(None, None, None)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

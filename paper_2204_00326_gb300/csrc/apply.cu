@@ -46,6 +46,8 @@ struct V2<float> {
 constexpr int kWarpsPerCta = 8;
 constexpr int kMaxPass = 12;        // passes in one launch group
 constexpr int kMaxRhs = 64;         // right-hand sides of one application
+constexpr int kFlagDirectHost = 1 << 8;  // same bits as the device-side record flags
+constexpr int kFlagAddHost = 1 << 9;
 constexpr long kChunkElems = 1024;  // matrix entries per chunk (8 KB in complex64)
 
 template <typename T>
@@ -130,8 +132,51 @@ __device__ __forceinline__ const char* chunk_src(const GroupArgs<T>& g, const in
     using C = typename V2<T>::t;
     const PassArgs<T>& pa = g.p[a.x & 0xff];
     const long elem = (long)(unsigned)b.x | ((long)b.y << 32);
-    bytes = (unsigned)((size_t)b.z * sizeof(C));
+    const int ro = (a.x >> 16) & 0xffff;
+    bytes = (unsigned)((size_t)a.z * (ro + (ro & 1)) * sizeof(C));
     return (const char*)(pa.mats + elem);
+}
+
+// Record flags (bits of a.x above the pass index).
+constexpr int kFlagDirect = 1 << 8;  // the row's only chunk: write y itself
+constexpr int kFlagAdd = 1 << 9;     // add to y (it already holds this application's values)
+
+// Partial slots of a row split over chunks [c0, c1): c0 and every k * kpw
+// inside (c0, c1), one per chunk range that touches the row.
+__device__ __forceinline__ int row_slots(int c0, int c1, int kpw) { return 1 + ((c1 - 1) / kpw - c0 / kpw); }
+
+// A warp that wrote its partial of a split row counts in; the last of the
+// row's writers sums every partial in slot order (so the result does not
+// depend on which warp finishes last) into y, and re-arms the counter.
+template <typename T>
+__device__ __forceinline__ void finish_row(typename V2<T>::t* y, const typename V2<T>::t* P, int Pld, int* cnt, int c0, int c1, int kpw,
+                                           int ro, bool add, int lane)
+{
+    using C = typename V2<T>::t;
+    __threadfence();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&cnt[c0], 1) + 1 == row_slots(c0, c1, kpw);
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    for (int i = lane; i < ro; i += 32) {
+        T sr = 0, si = 0;
+        if (add) {
+            const C o = y[i];
+            sr = o.x;
+            si = o.y;
+        }
+        for (int c = c0; c < c1; c = (c / kpw + 1) * kpw) {
+            const C p = __ldcg(&P[(size_t)c * Pld + i]);
+            sr += p.x;
+            si += p.y;
+        }
+        C o;
+        o.x = sr;
+        o.y = si;
+        y[i] = o;
+    }
+    if (lane == 0) cnt[c0] = 0;
 }
 
 // Load (into registers) the input coefficients of the chunk described by a.
@@ -336,7 +381,7 @@ __device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typenam
 template <typename T>
 __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(int nch, int kpw, const int4* __restrict__ recs,
                                                                    const __grid_constant__ GroupArgs<T> g,
-                                                                   typename V2<T>::t* __restrict__ P, int Pld, int accumulate,
+                                                                   typename V2<T>::t* __restrict__ P, int Pld, int* __restrict__ cnt,
                                                                    int* __restrict__ err)
 {
     using C = typename V2<T>::t;
@@ -417,9 +462,16 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(int nch, int 
         // end of this row's run in the range: write it out
         const bool row_ends = (c + 1 == ce) || na.x != ra.x || na.y != ra.y;
         if (row_ends) {
-            const bool direct = (ra.x >> 8) & 1;
-            C* dst = direct ? pa.y + (size_t)ra.y * pa.ldy : P + (size_t)pslot * Pld;
-            flush_row<T>(acc, ro, lane, dst, direct, accumulate);
+            const bool direct = (ra.x & kFlagDirect) != 0;
+            const bool add = (ra.x & kFlagAdd) != 0;
+            C* yrow = pa.y + (size_t)ra.y * pa.ldy;
+            // rows whose every chunk lies in this warp's range need no partials
+            if (direct || (rb.w >= cb && rb.z <= ce)) {
+                flush_row<T>(acc, ro, lane, yrow, true, add);
+            } else {
+                flush_row<T>(acc, ro, lane, P + (size_t)pslot * Pld, false, 0);
+                finish_row<T>(yrow, P, Pld, cnt, rb.w, rb.z, kpw, ro, add, lane);
+            }
             acc.zero();
             pslot = c + 1;
         }
@@ -452,11 +504,12 @@ struct BatchCfg {
 template <typename T, int MR>
 __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, int nrhs, int nrhs_pad, const int4* __restrict__ recs,
                                                              const __grid_constant__ GroupArgs<T> g,
-                                                             typename V2<T>::t* __restrict__ P, int Pld, int accumulate,
+                                                             typename V2<T>::t* __restrict__ P, int Pld, int* __restrict__ cnt,
                                                              int* __restrict__ err)
 {
     using C = typename V2<T>::t;
     extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto stage = [&](int k) { return (C*)(smem + (size_t)k * BatchCfg<T>::kStage); };
     C* xs = (C*)(smem + 2 * BatchCfg<T>::kStage);
@@ -541,16 +594,20 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
         }
         const bool row_ends = (c + 1 == ce) || recs[2 * (c + 1)].x != ra.x || recs[2 * (c + 1)].y != ra.y;
         if (row_ends) {
-            const bool direct = (ra.x >> 8) & 1;
+            const bool direct = (ra.x & kFlagDirect) != 0;
+            const bool add = (ra.x & kFlagAdd) != 0;
+            C* yrow = pa.y + (size_t)ra.y * pa.ldy * nrhs;
+            const int4 rbx = recs[2 * c + 1];
+            const bool whole = direct || (rbx.w >= cb && rbx.z <= ce);  // every chunk of the row is in this CTA's range
             if (r < nrhs) {
-                C* dst = direct ? pa.y + (size_t)ra.y * pa.ldy * nrhs : P + (size_t)pslot * Pld * nrhs;
+                C* dst = whole ? yrow : P + (size_t)pslot * Pld * nrhs;
 #pragma unroll
                 for (int m = 0; m < MR; m++) {
                     const int i = i0 + m;
                     if (i < ro && m < h) {
                         C* q = dst + (size_t)i * nrhs + r;
                         T re = ar[m], im = ai[m];
-                        if (direct && accumulate) {
+                        if (whole && add) {
                             const C o = *q;
                             re += o.x;
                             im += o.y;
@@ -562,6 +619,36 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
                     }
                     ar[m] = ai[m] = 0;
                 }
+            }
+            if (!whole) {
+                // the last CTA to write a partial of this row sums them in slot order
+                const int c0 = rbx.w, c1 = rbx.z;
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) s_last = atomicAdd(&cnt[c0], 1) + 1 == row_slots(c0, c1, kpc);
+                __syncthreads();
+                if (s_last) {
+                    __threadfence();
+                    for (int qq = tid; qq < ro * nrhs; qq += blockDim.x) {
+                        T sr = 0, si = 0;
+                        if (add) {
+                            const C o = yrow[qq];
+                            sr = o.x;
+                            si = o.y;
+                        }
+                        for (int cc = c0; cc < c1; cc = (cc / kpc + 1) * kpc) {
+                            const C p = __ldcg(&P[(size_t)cc * Pld * nrhs + qq]);
+                            sr += p.x;
+                            si += p.y;
+                        }
+                        C o;
+                        o.x = sr;
+                        o.y = si;
+                        yrow[qq] = o;
+                    }
+                    if (tid == 0) cnt[c0] = 0;
+                }
+                __syncthreads();
             }
             pslot = c + 1;
         }
@@ -672,47 +759,90 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) reduce_kernel(int nrows, in
 }
 
 // out = v + kappa^2 q (U_B u^{B,i} + sum_{9 offsets} T_o v_{B+o}) per leaf.
-// 16 threads per leaf (one per node), 8 leaves per CTA.  Near blocks are
-// stored [o][j][i] (target index fastest) for conflict-free shared reads.
+// 48 threads per leaf: node i and one row sy of the 3 x 3 near offsets each;
+// the third group also does L2P; the groups' sums meet in shared memory.
+// 4 leaves per CTA.  Near blocks are stored [o][j][i] (target index fastest)
+// for conflict-free shared reads.
+constexpr int kLeafPerCta = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(128) leaf_apply_kernel(int nleaf, const int* __restrict__ nbr,
-                                                         const typename V2<T>::t* __restrict__ near,
-                                                         const typename V2<T>::t* __restrict__ vin,
-                                                         const int* __restrict__ l2p_rowptr, const long* __restrict__ l2p_moff,
-                                                         const int* __restrict__ l2p_rin,
-                                                         const typename V2<T>::t* __restrict__ l2p, int ldl,
-                                                         const typename V2<T>::t* __restrict__ lc,
-                                                         const double2* __restrict__ v, const double* __restrict__ q, double k2,
-                                                         double2* __restrict__ out)
+__global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf, const int* __restrict__ nbr,
+                                                                      const typename V2<T>::t* __restrict__ near,
+                                                                      const typename V2<T>::t* __restrict__ vin,
+                                                                      const int* __restrict__ l2p_rowptr, const long* __restrict__ l2p_moff,
+                                                                      const int* __restrict__ l2p_rin,
+                                                                      const typename V2<T>::t* __restrict__ l2p, int ldl,
+                                                                      const typename V2<T>::t* __restrict__ lc,
+                                                                      const double2* __restrict__ v, const double* __restrict__ q, double k2,
+                                                                      double2* __restrict__ out)
 {
     using C = typename V2<T>::t;
-    __shared__ C sn[9 * 256];
-    for (int k = threadIdx.x; k < 9 * 256; k += blockDim.x) sn[k] = near[k];
-    __syncthreads();
-    const int leaf = blockIdx.x * 8 + (threadIdx.x >> 4);
-    const int i = threadIdx.x & 15;
-    if (leaf >= nleaf) return;
-    T ar = 0, ai = 0;
-#pragma unroll 1
-    for (int o = 0; o < 9; o++) {
-        const int src = nbr[leaf * 9 + o];
-        if (src < 0) continue;
-        const C* vs = vin + (size_t)src * 16;
-        const C* B = sn + o * 256 + i;
+    __shared__ __align__(16) C sn[9 * 256];
+    __shared__ C part[2][kLeafPerCta * 16];
+    {
+        // 16-byte loads, all issued before any is used
+        constexpr int kVec = 9 * 256 * (int)sizeof(C) / 16;
+        constexpr int kPer = (kVec + 48 * kLeafPerCta - 1) / (48 * kLeafPerCta);
+        const uint4* src = (const uint4*)near;
+        uint4* dst = (uint4*)sn;
+        uint4 tmp[kPer];
 #pragma unroll
-        for (int j = 0; j < 16; j++) cmac<T>(ar, ai, B[j * 16], vs[j]);
+        for (int u = 0; u < kPer; u++) {
+            const int k = threadIdx.x + u * 48 * kLeafPerCta;
+            if (k < kVec) tmp[u] = src[k];
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+            const int k = threadIdx.x + u * 48 * kLeafPerCta;
+            if (k < kVec) dst[k] = tmp[u];
+        }
     }
-    if (l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {
-        const int e = l2p_rowptr[leaf];
-        const C* U = l2p + l2p_moff[e] + i;
-        const C* u = lc + (size_t)leaf * ldl;
-        const int ri = l2p_rin[e];
-        for (int j = 0; j < ri; j++) cmac<T>(ar, ai, U[j * 16], u[j]);
+    __syncthreads();
+    const int grp = threadIdx.x / (16 * kLeafPerCta);  // offset row sy = grp - 1
+    const int li = threadIdx.x % (16 * kLeafPerCta);
+    const int leaf = blockIdx.x * kLeafPerCta + li / 16;
+    const int i = li & 15;
+    T ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
+    if (leaf < nleaf) {
+#pragma unroll
+        for (int sx = 0; sx < 3; sx++) {
+            const int o = grp * 3 + sx;
+            const int src = nbr[leaf * 9 + o];
+            if (src < 0) continue;
+            const C* vs = vin + (size_t)src * 16;
+            const C* B = sn + o * 256 + i;
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                cmac<T>(ar0, ai0, B[j * 16], vs[j]);
+                cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
+            }
+        }
+        if (grp == 2 && l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {
+            const int e = l2p_rowptr[leaf];
+            const C* U = l2p + l2p_moff[e] + i;
+            const C* u = lc + (size_t)leaf * ldl;
+            const int ri = l2p_rin[e];
+            int j = 0;
+            for (; j + 1 < ri; j += 2) {
+                cmac<T>(ar0, ai0, U[j * 16], u[j]);
+                cmac<T>(ar1, ai1, U[(j + 1) * 16], u[j + 1]);
+            }
+            if (j < ri) cmac<T>(ar0, ai0, U[j * 16], u[j]);
+        }
     }
-    const size_t gi = (size_t)leaf * 16 + i;
-    const double2 vv = v[gi];
-    const double s = k2 * q[gi];
-    out[gi] = make_double2(vv.x + s * (double)ar, vv.y + s * (double)ai);
+    C mine;
+    mine.x = ar0 + ar1;
+    mine.y = ai0 + ai1;
+    if (grp > 0) part[grp - 1][li] = mine;
+    __syncthreads();
+    if (grp == 0 && leaf < nleaf) {
+        const C a = part[0][li], b = part[1][li];
+        const T sr = mine.x + a.x + b.x, si = mine.y + a.y + b.y;
+        const size_t gi = (size_t)leaf * 16 + i;
+        const double2 vv = v[gi];
+        const double sc = k2 * q[gi];
+        out[gi] = make_double2(vv.x + sc * (double)sr, vv.y + sc * (double)si);
+    }
 }
 
 __global__ void to_c64_kernel(long n, const double2* __restrict__ a, float2* __restrict__ b)
@@ -794,7 +924,7 @@ void free_bsr(BsrDev& d)
 // row with exactly one chunk is written by that chunk directly; the others
 // are listed for the reduction.  ldx: stride of the pass's input buffer.
 void build_group(Group& g, const std::vector<PassRef>& passes, const std::vector<const BsrHost*>& hs, const std::vector<int>& ldx,
-                 int accumulate)
+                 int accumulate, const std::vector<char>* initialized = nullptr)
 {
     if (passes.size() > (size_t)kMaxPass) fail(DAFMM_EBADARG, "too many passes in one launch group");
     g.passes = passes;
@@ -818,17 +948,15 @@ void build_group(Group& g, const std::vector<PassRef>& passes, const std::vector
             const int ldr = b.ld[r];
             const int per = (int)std::max<long>(1, std::min<long>(kMaxChunkCols, kChunkElems / ldr));
             const int c0 = (int)(recs.size() / 2);
+            const int nck = (J + per - 1) / per;
+            // add to y only where this application already wrote the row
+            const int add = (accumulate && (!initialized || (*initialized)[r])) ? kFlagAddHost : 0;
             for (int j = 0; j < J; j += per) {
                 const int j1 = std::min(J, j + per);
                 const long elem = rbase[r] + (long)j * ldr;
-                recs.push_back(make_int4((int)p | (ro << 16), r, j1 - j, cbase[r] + j));
-                recs.push_back(make_int4((int)(elem & 0xffffffffL), (int)(elem >> 32), (j1 - j) * ldr, c0));
+                recs.push_back(make_int4((int)p | add | (nck == 1 ? kFlagDirectHost : 0) | (ro << 16), r, j1 - j, cbase[r] + j));
+                recs.push_back(make_int4((int)(elem & 0xffffffffL), (int)(elem >> 32), c0 + nck, c0));
             }
-            const int c1 = (int)(recs.size() / 2);
-            if (c1 - c0 == 1)
-                recs[2 * c0].x |= 1 << 8;  // the row's only chunk writes the row
-            else if (!(accumulate && c1 == c0))
-                rows.push_back(make_int4((int)p, r, c0, c1));
         }
         long* drb = nullptr;
         int* dcb = nullptr;
@@ -845,12 +973,15 @@ void build_group(Group& g, const std::vector<PassRef>& passes, const std::vector
     g.Pld = std::max(pld, 1);
     upload_vec(recs, &g.chunks);
     upload_vec(rows, &g.rows);
+    std::vector<int> zeros(std::max(g.nch, 1), 0);
+    upload_vec(zeros, &g.cnt);
 }
 
 void free_group(Group& g)
 {
     cudaFree(g.chunks);
     cudaFree(g.rows);
+    cudaFree(g.cnt);
     for (long* p : g.rbase) cudaFree(p);
     for (int* p : g.cbase) cudaFree(p);
     for (int* p : g.xmap) cudaFree(p);
@@ -919,8 +1050,8 @@ void launch_group(const Tree& t, const OpsDev& d, const Bufs<T>& b, const typena
         const int ctas = std::max(1, std::min((g.nch + kStreamWarps - 1) / kStreamWarps, sms * psm));
         const int warps = ctas * kStreamWarps;
         kpw = (g.nch + warps - 1) / warps;
-        stream_kernel<T><<<(unsigned)ctas, 32 * kStreamWarps, StreamCfg<T>::kCta, s>>>(g.nch, kpw, g.chunks, ga, b.part, g.Pld,
-                                                                                       g.accumulate, d.err);
+        stream_kernel<T><<<(unsigned)ctas, 32 * kStreamWarps, StreamCfg<T>::kCta, s>>>(g.nch, kpw, g.chunks, ga, b.part, g.Pld, g.cnt,
+                                                                                       d.err);
     }
     if (g.nrows > 0)
         reduce_kernel<T><<<(unsigned)((g.nrows + kWarpsPerCta - 1) / kWarpsPerCta), 32 * kWarpsPerCta, 0, s>>>(
@@ -984,7 +1115,7 @@ void run(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, const do
     mark(prof, 3, s);
     const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
     const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
-    leaf_apply_kernel<T><<<(unsigned)((nleaf + 7) / 8), 128, 0, s>>>(
+    leaf_apply_kernel<T><<<(unsigned)((nleaf + kLeafPerCta - 1) / kLeafPerCta), 48 * kLeafPerCta, 0, s>>>(
         nleaf, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
         l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
         (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
@@ -1014,7 +1145,7 @@ void launch_batched_mr(const OpsDev& d, const Group& g, const GroupArgs<T>& ga, 
         kpc = (g.nch + ctas - 1) / ctas;
         const int grid = (g.nch + kpc - 1) / kpc;
         stream_batched_kernel<T, MR><<<(unsigned)grid, threads, smem, s>>>(g.nch, kpc, nrhs, nrhs_pad, g.chunks, ga, part, g.Pld,
-                                                                         g.accumulate, d.err);
+                                                                         g.cnt, d.err);
     }
     if (g.nrows > 0)
         reduce_batched_kernel<T><<<(unsigned)g.nrows, 256, 0, s>>>(g.nrows, kpc, nrhs, g.rows, ga, part, g.Pld, g.accumulate);
@@ -1102,7 +1233,13 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
             d.lv[nu].Ri = h.lv[nu].Ri;
             d.lv[nu].Ro = h.lv[nu].Ro;
             build_group(d.up[nu], {PassRef{nu, 0}}, {&h.lv[nu].up}, {nu == L ? 16 : h.lv[nu + 1].Ro}, 0);
-            if (nu < L) build_group(d.down[nu], {PassRef{nu, 2}}, {&h.lv[nu].down}, {h.lv[nu].Ri}, 1);
+            if (nu < L) {
+                // rows of level nu+1 that its M2L writes in every application
+                const BsrHost& mc = h.lv[nu + 1].m2l;
+                std::vector<char> init(mc.nrows, 0);
+                for (int r = 0; r < mc.nrows; r++) init[r] = mc.rowptr[r + 1] > mc.rowptr[r];
+                build_group(d.down[nu], {PassRef{nu, 2}}, {&h.lv[nu].down}, {h.lv[nu].Ri}, 1, &init);
+            }
             m2l_passes.push_back(PassRef{nu, 1});
             m2l_hosts.push_back(&h.lv[nu].m2l);
             m2l_ldx.push_back(h.lv[nu].Ro);
@@ -1247,6 +1384,13 @@ int sync_and_check(OpsDev& d, cudaStream_t stream)
     int flag = 0;
     CK(cudaMemcpy(&flag, d.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
+        // a warp that gave up may have left split-row counters armed
+        auto rearm = [](Group& g) {
+            if (g.cnt) CK(cudaMemset(g.cnt, 0, sizeof(int) * std::max(g.nch, 1)));
+        };
+        for (auto& g : d.up) rearm(g);
+        for (auto& g : d.down) rearm(g);
+        rearm(d.m2l);
         CK(cudaMemset(d.err, 0, sizeof(int)));
         return DAFMM_ETIMEOUT;
     }

@@ -38,6 +38,7 @@ struct Group {
     int4* chunks = nullptr;  // two int4 per chunk (a column range of a row's matrix), see apply.cu
     int4* rows = nullptr;    // {pass, row, chunk0, chunk1}
     int accumulate = 0;      // add into y instead of overwriting
+    int* cnt = nullptr;      // per chunk: writers of a split row's partials seen so far
     // per pass: element offset of each row's matrix, offset of each row's
     // columns in xmap, and for every column the index of its input coefficient
     std::vector<long*> rbase;

@@ -104,7 +104,13 @@ typedef struct dafmm_stats_t {
     int launches_per_call_fp64;   /* ... in FP64 */
 } dafmm_stats_t;
 
-/* Device time of the passes of the profiled dafmm_matvec calls (ms, summed). */
+/*
+ * Device time of the passes of the profiled dafmm_matvec calls (ms, summed).
+ * A single-right-hand-side call runs every tree pass (P2M, M2M, M2L, L2L) in
+ * one kernel: it adds to ms_far only.  A call with several right-hand sides
+ * launches the passes separately: it adds to ms_up, ms_m2l and ms_down, and
+ * their sum to ms_far.
+ */
 typedef struct dafmm_profile_t {
     long calls;
     double ms_total;  /* first to last kernel of each call */
@@ -112,6 +118,7 @@ typedef struct dafmm_profile_t {
     double ms_m2l;    /* M2L at every level */
     double ms_down;   /* L2L into the leaves' locals */
     double ms_leaf;   /* L2P + near field + epilogue */
+    double ms_far;    /* every tree pass: P2M, M2M, M2L, L2L */
 } dafmm_profile_t;
 
 typedef struct dafmm_tree dafmm_tree;
@@ -298,12 +305,26 @@ int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v_dev, double* out_
 
 /*
  * dafmm_sync -- synchronise the stream, then report whether any kernel of
- * this handle gave up a bounded wait on a device-side barrier since the last
- * check (DAFMM_ETIMEOUT; the flag is cleared).  Otherwise DAFMM_OK, or
- * DAFMM_ECUDA for a CUDA error.  The apply kernels wait on the arrival of
- * their own bulk copies with an iteration limit instead of an unbounded spin.
+ * this handle gave up a bounded wait on the device since the last check
+ * (DAFMM_ETIMEOUT; the flag is cleared).  Otherwise DAFMM_OK, or DAFMM_ECUDA
+ * for a CUDA error.  The apply kernels wait with a limit instead of an
+ * unbounded spin: on the arrival of their own bulk copies (an iteration
+ * limit) and, in the single-right-hand-side launch, on the rows of the tree
+ * passes they read (about 0.2 s each).  After a timeout the result of the
+ * application is undefined; the handle stays usable.
  */
 int dafmm_sync(dafmm_ops* ops, void* stream);
+
+/*
+ * dafmm_debug_stall -- test support for the timeout path (the paper has no
+ * counterpart).  The next single-right-hand-side dafmm_matvec on this handle
+ * runs without graph replay and its kernel waits for one more row of tree
+ * pass `pass` (0 = the leaf-level P2M) than the pass writes, so that wait
+ * and the waits behind it give up; dafmm_sync then returns DAFMM_ETIMEOUT.
+ * pass = -1 cancels.  Errors: DAFMM_EBADARG for a NULL handle or a pass
+ * outside -1 .. (passes - 1).
+ */
+int dafmm_debug_stall(dafmm_ops* ops, int pass);
 
 /* Realised ranks, operator bytes and work of one application. */
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats);

@@ -331,9 +331,18 @@ int dafmm_sync(dafmm_ops* ops, void* stream)
     int r = guarded([&] {
         if (!ops) fail(DAFMM_EBADARG, "NULL argument");
         st = sync_and_check(ops->dev, (cudaStream_t)stream);
-        if (st == DAFMM_ETIMEOUT) fail(DAFMM_ETIMEOUT, "a device-side wait gave up (bulk copy did not arrive in time)");
+        if (st == DAFMM_ETIMEOUT) fail(DAFMM_ETIMEOUT, "a device-side wait gave up (a bulk copy or a tree pass did not arrive in time)");
     });
     return r;
+}
+
+int dafmm_debug_stall(dafmm_ops* ops, int pass)
+{
+    return guarded([&] {
+        if (!ops) fail(DAFMM_EBADARG, "NULL argument");
+        if (pass < -1 || pass >= (int)ops->dev.fz.g.passes.size()) fail(DAFMM_EBADARG, "pass out of range");
+        ops->dev.stall_pass = pass;
+    });
 }
 
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats)

@@ -20,11 +20,17 @@ struct LevelDev {
     void* lc64 = nullptr;
     void* mp32 = nullptr;
     void* lc32 = nullptr;
+    // single right-hand side, [0] complex128, [1] complex64: multipoles, locals
+    // from M2L, locals from the parent (L2L); rows no pass writes stay zero
+    void* fmp[2] = {};
+    void* flc[2] = {};
+    void* flcd[2] = {};
 };
 
 // Block-sparse passes launched together: their rows are cut into chunks of
-// at most a few thousand block entries, one warp per chunk; a second kernel
-// sums each row's chunk partials in a fixed order.
+// at most a thousand block entries; chunk ranges go to warps (one right-hand
+// side) or CTAs (several), and the last writer of a split row sums its
+// partials in a fixed order.
 struct PassRef {
     int level = 0;
     int kind = 0;  // 0 up (P2M/M2M), 1 M2L, 2 down (L2L)
@@ -33,10 +39,8 @@ struct PassRef {
 struct Group {
     std::vector<PassRef> passes;
     int nch = 0;             // chunks
-    int nrows = 0;           // rows summed by the reduction
     int Pld = 0;             // stride of a chunk's partial (largest row rank)
     int4* chunks = nullptr;  // two int4 per chunk (a column range of a row's matrix), see apply.cu
-    int4* rows = nullptr;    // {pass, row, chunk0, chunk1}
     int accumulate = 0;      // add into y instead of overwriting
     int* cnt = nullptr;      // per chunk: writers of a split row's partials seen so far
     // per pass: element offset of each row's matrix, offset of each row's
@@ -44,6 +48,20 @@ struct Group {
     std::vector<long*> rbase;
     std::vector<int*> cbase;
     std::vector<int*> xmap;
+};
+
+// Every tree pass of a single-right-hand-side application in one cooperative
+// launch.  Chunks are ordered by phase; a warp takes an equal share of every
+// phase in turn, and before the first chunk of a pass it waits until the
+// passes it reads have written all their rows (per-pass row counters).
+struct Fused {
+    Group g;                      // passes, chunks (phase by phase), partial counters
+    std::vector<unsigned> deps;   // per pass: bit mask of the passes whose output it reads
+    std::vector<int> target;      // per pass: rows it writes
+    std::vector<int> base;        // per phase: first chunk; base[nph] = chunks
+    int nph = 0;
+    int ctas[2] = {0, 0};         // persistent grid, [0] complex128, [1] complex64
+    int* done = nullptr;          // per pass: rows written in the running application
 };
 
 // One captured application (per precision), replayed while the vector
@@ -64,6 +82,7 @@ struct OpsDev {
     std::vector<Group> up;      // per level (index = level)
     Group m2l;                  // every level at once
     std::vector<Group> down;    // per level (index = parent level)
+    Fused fz;                   // single right-hand side: every pass in one launch
     double2* near64 = nullptr;  // 9 x 16 x 16, source offset (sx,sy) -> (sy+1)*3+(sx+1)
     float2* near32 = nullptr;
     int* nbr = nullptr;         // [nleaf][9] source leaf of each near offset, -1 outside
@@ -73,9 +92,12 @@ struct OpsDev {
     size_t part_elems = 0;      // complex elements per right-hand side in part
     int nrhs_cap = 0;           // scratch sized for this many right-hand sides
     int* err = nullptr;         // device flag: a bounded wait in a kernel gave up
-    // per-pass timing: 5 events per profiled call (start, up, m2l, down, leaf)
+    int stall_pass = -1;        // test support: the next fused launch waits for a row this pass never writes
+    // per-pass timing: 5 events per profiled call (start, up, m2l, down, leaf);
+    // for a fused call the first interval holds the whole far field
     bool profile = false;
     std::vector<cudaEvent_t> events;
+    std::vector<char> ev_fused;  // per profiled call
     size_t ev_used = 0;
     // graph replay
     cudaStream_t cap_stream = nullptr;   // private stream used only for capture

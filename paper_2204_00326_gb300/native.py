@@ -90,6 +90,7 @@ class dafmm_profile_t(ctypes.Structure):
         ("ms_m2l", ctypes.c_double),
         ("ms_down", ctypes.c_double),
         ("ms_leaf", ctypes.c_double),
+        ("ms_far", ctypes.c_double),
     ]
 
 
@@ -134,6 +135,7 @@ _sig = {
     "dafmm_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
+    "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
     "gmres_solve": ([_P, _P, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
     "hodlr_factor": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hodlr_solve": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -247,6 +249,13 @@ def dafmm_matvec_noalloc(ops: int, v, out, precision: int = DAFMM_FP64, stream=N
 def dafmm_sync(ops: int, stream=None) -> None:
     """Synchronise and raise DafmmError(DAFMM_ETIMEOUT) if a device wait gave up."""
     _check(lib.dafmm_sync(ops, _stream_ptr(stream)))
+
+
+def dafmm_debug_stall(ops: int, pass_index: int) -> None:
+    """Test support: the next single-RHS application waits for a row of tree
+    pass `pass_index` that is never written (bounded), so dafmm_sync reports
+    DAFMM_ETIMEOUT.  -1 cancels."""
+    _check(lib.dafmm_debug_stall(ops, int(pass_index)))
 
 
 def dafmm_stats(ops: int) -> dafmm_stats_t:

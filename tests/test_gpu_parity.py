@@ -8,6 +8,8 @@ entry to 6e-8 relative, and the realised NCA factors amplify that by the
 norms of the interpolation operators (|U|, |V| up to ~1e2), giving a few 1e-6
 on the matvec; refinement in FP64 removes it in the solver.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -151,8 +153,19 @@ def test_profile_records_passes(N, op128):
         op128.matvec(v, precision=N.DAFMM_MIXED)
     p = N.dafmm_profile_read(op128.ops)
     N.dafmm_profile(op128.ops, False)
-    assert p.calls == 3 and p.ms_m2l > 0 and p.ms_leaf > 0
-    assert abs(p.ms_total - (p.ms_up + p.ms_m2l + p.ms_down + p.ms_leaf)) < 1e-6
+    # one right-hand side: every tree pass is one kernel, reported as the far field only
+    assert p.calls == 3 and p.ms_far > 0 and p.ms_leaf > 0
+    assert p.ms_up == 0 and p.ms_m2l == 0 and p.ms_down == 0
+    assert abs(p.ms_total - (p.ms_far + p.ms_leaf)) < 1e-6
+    # several right-hand sides: the passes are launched separately
+    V = torch.as_tensor(W.random_vector(op128.N, 4, seed=3), device="cuda").contiguous()
+    N.dafmm_profile(op128.ops, True)
+    op128.matvec(V, precision=N.DAFMM_MIXED)
+    p = N.dafmm_profile_read(op128.ops)
+    N.dafmm_profile(op128.ops, False)
+    assert p.calls == 1 and p.ms_m2l > 0 and p.ms_up > 0 and p.ms_down > 0
+    assert abs(p.ms_far - (p.ms_up + p.ms_m2l + p.ms_down)) < 1e-6
+    assert abs(p.ms_total - (p.ms_far + p.ms_leaf)) < 1e-6
 
 
 def test_graph_replay_follows_new_pointers(N, op128):
@@ -209,3 +222,24 @@ def test_batched_rejects_too_many_rhs(N, op128):
     V = torch.zeros(op128.N, 65, dtype=torch.complex128, device="cuda")
     with pytest.raises(N.DafmmError):
         op128.matvec(V)
+
+
+def test_stalled_pass_times_out_and_handle_recovers(N, op128):
+    """A tree pass that never completes: the bounded waits give up, the host
+    reads DAFMM_ETIMEOUT, and the next application is correct again."""
+    v = torch.as_tensor(W.random_vector(op128.N, 1, seed=77)[:, 0], device="cuda")
+    ref = op128.matvec(v, precision=N.DAFMM_MIXED)
+    op128.sync()
+    with pytest.raises(N.DafmmError):
+        N.dafmm_debug_stall(op128.ops, 10 ** 6)
+    N.dafmm_debug_stall(op128.ops, 0)
+    out = torch.empty_like(v)
+    t0 = time.perf_counter()
+    N.dafmm_matvec(op128.ops, v, out, N.DAFMM_MIXED)
+    with pytest.raises(N.DafmmError) as e:
+        op128.sync()
+    assert e.value.code == N.DAFMM_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    again = op128.matvec(v, precision=N.DAFMM_MIXED)
+    op128.sync()
+    assert torch.equal(again, ref)

@@ -917,10 +917,12 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
 // 48 threads per leaf: node i and one row sy of the 3 x 3 near offsets each;
 // the third group also does L2P; the groups' sums meet in shared memory.
 // 4 leaves per CTA.  Near blocks are stored [o][j][i] (target index fastest)
-// for conflict-free shared reads.  The input is read in complex128 and
-// rounded to T; the leaves' locals are lc (+ lc2 when not null).  done (not
-// null): row counters of the fused launch before, reset here for the next
-// application.
+// for conflict-free shared reads.  A CTA's four leaves are consecutive in
+// Morton order (a 2 x 2 quad); the inputs of the 4 x 4 leaves around it are
+// read in complex128, rounded to T once and kept in shared memory (FP64
+// conversions are scarce on this GPU).  The leaves' locals are lc (+ lc2 when
+// not null).  done (not null): row counters of the fused launch before,
+// reset here for the next application.
 constexpr int kLeafPerCta = 4;
 
 template <typename T>
@@ -935,9 +937,31 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
                                                                       double2* __restrict__ out, int* __restrict__ done, int npass)
 {
     using C = typename V2<T>::t;
+    static_assert(kLeafPerCta == 4, "a CTA takes one 2 x 2 quad of leaves (four consecutive Morton indices)");
     __shared__ __align__(16) C sn[9 * 256];
+    __shared__ __align__(16) C vq[16][16];  // inputs of the 4 x 4 leaves around the quad, rounded to T once
     __shared__ C part[2][kLeafPerCta * 16];
     if (done != nullptr && blockIdx.x == 0 && threadIdx.x < npass) done[threadIdx.x * kDoneStride] = 0;
+    auto rnd = [](double2 d) {
+        C c;
+        c.x = (T)d.x;
+        c.y = (T)d.y;
+        return c;
+    };
+    const int q0 = blockIdx.x * kLeafPerCta;
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        // block position (bx, by) seen from quad leaf l = (bx >= 2) + 2 (by >= 2) at offset (sx, sy)
+        const int pos = t >> 4, j = t & 15;
+        const int bx = pos & 3, by = pos >> 2;
+        const int l = (bx >= 2 ? 1 : 0) | (by >= 2 ? 2 : 0);
+        const int sx = bx - 1 - (l & 1), sy = by - 1 - (l >> 1);
+        const int src = q0 + l < nleaf ? nbr[(q0 + l) * 9 + (sy + 1) * 3 + (sx + 1)] : -1;
+        C val;
+        val.x = 0;
+        val.y = 0;
+        if (src >= 0) val = rnd(v[(size_t)src * 16 + j]);
+        vq[pos][j] = val;
+    }
     {
         // 16-byte loads, all issued before any is used
         constexpr int kVec = 9 * 256 * (int)sizeof(C) / 16;
@@ -962,24 +986,17 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
     const int leaf = blockIdx.x * kLeafPerCta + li / 16;
     const int i = li & 15;
     T ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
-    auto rnd = [](double2 d) {
-        C c;
-        c.x = (T)d.x;
-        c.y = (T)d.y;
-        return c;
-    };
     if (leaf < nleaf) {
+        const int l = leaf - q0;
 #pragma unroll
         for (int sx = 0; sx < 3; sx++) {
-            const int o = grp * 3 + sx;
-            const int src = nbr[leaf * 9 + o];
-            if (src < 0) continue;
-            const double2* vs = v + (size_t)src * 16;
+            const int o = grp * 3 + sx;  // offset (sx - 1, grp - 1); outside the domain vq holds zeros
+            const C* vs = vq[(1 + (l >> 1) + grp - 1) * 4 + 1 + (l & 1) + sx - 1];
             const C* B = sn + o * 256 + i;
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
-                cmac<T>(ar0, ai0, B[j * 16], rnd(vs[j]));
-                cmac<T>(ar1, ai1, B[(j + 1) * 16], rnd(vs[j + 1]));
+                cmac<T>(ar0, ai0, B[j * 16], vs[j]);
+                cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
             }
         }
         if (grp == 2 && l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {

@@ -67,12 +67,19 @@ struct PassArgs {
 // Schedule of the fused launch: phases of the chunk list and the pass
 // dependencies (see Fused in ops.h).
 struct Sched {
+    // chain list: the passes without slack, phase by phase, in static warp shares
     int nph;
-    int base[kMaxPhase + 1];   // first chunk of each phase; base[nph] = chunks
-    int kpw[kMaxPhase];        // chunks per warp in each phase
-    int sbase[kMaxPhase];      // warp shares in the phases before
-    unsigned deps[kMaxPass];   // per pass: passes whose rows it reads
-    int target[kMaxPass];      // per pass: rows it writes
+    int base[kMaxPhase + 1];    // first chunk of each phase; base[nph] = chain chunks
+    int kpw[kMaxPhase];         // chunks per warp in each phase
+    int sbase[kMaxPhase];       // warp shares in the phases before (partial slots)
+    unsigned phdeps[kMaxPhase]; // passes read by the passes of each phase
+    // bulk list: the passes with slack, cut into pieces handed out in order
+    int npieces;
+    const int4* pieces;         // per piece: {first chunk, end chunk, partial slot, pass}
+    int* next_piece;            // piece counter
+    unsigned deps[kMaxPass];    // per pass: passes whose rows it reads
+    int target[kMaxPass];       // per pass: rows it writes
+    int dphase[kMaxPass];       // per pass: latest phase among the passes it reads (-1: none)
 };
 
 template <typename T>
@@ -162,6 +169,13 @@ __host__ __device__ __forceinline__ int row_slots(int c0, int c1, int base, int 
     return 1 + ((c1 - 1 - base) / kpw - (c0 - base) / kpw);
 }
 __device__ __forceinline__ int next_slot(int c, int base, int kpw) { return base + ((c - base) / kpw + 1) * kpw; }
+
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 __device__ __forceinline__ void red_add_release(int* p, int v)
 {
@@ -508,13 +522,12 @@ __device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typenam
     }
 }
 
-// A warp's share of one phase of the fused chunk list: chunks [b, e), the
-// current one c.
+// A warp's share of one chain phase: chunks [b, e), the next to schedule c.
 struct Slice {
     int k, b, c, e;
 };
 
-// First non-empty share of warp w in phases k, k+1, ...
+// First non-empty share of warp w in chain phases k, k+1, ...
 __device__ __forceinline__ bool slice_from(const Sched& sc, int k, int w, Slice& sl)
 {
     for (; k < sc.nph; k++) {
@@ -531,25 +544,80 @@ __device__ __forceinline__ bool slice_from(const Sched& sc, int k, int w, Slice&
     return false;
 }
 
-__device__ __forceinline__ bool slice_next(const Sched& sc, int w, Slice& sl)
+constexpr int kPiece = 4;  // chunks per bulk piece
+
+// One scheduled chunk: c (-1: none); kind 0: chain (aux = phase, end = the
+// share's end), 1: bulk (aux = the piece's partial slot, end = the piece's end).
+struct Item {
+    int c, kind, aux, end;
+};
+
+__device__ __forceinline__ int ld_relaxed(const int* p)
 {
-    if (sl.c + 1 < sl.e) {
-        sl.c++;
-        return true;
-    }
-    return slice_from(sc, sl.k + 1, w, sl);
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Every tree pass of one application.  Each warp streams its share of every
-// phase through a two-stage TMA pipeline (the operator is static, so copies
-// run ahead of the data dependencies) and accumulates consecutive chunks of
-// one row in registers.  Before it gathers the inputs of a chunk of pass p it
-// makes sure the passes p reads are complete (bounded wait on their row
-// counters; a non-blocking poll while the previous chunk computes).  A row
-// whose chunks all lie in the warp's share is written directly; otherwise
-// the warp leaves a partial at its first chunk of the row and the last
-// writer sums them.  Every finished row moves its pass's counter.  Launched
-// cooperatively, so every warp is resident and the waits end.
+__device__ __forceinline__ int4 shfl4(int4 v)
+{
+    v.x = __shfl_sync(0xffffffffu, v.x, 0);
+    v.y = __shfl_sync(0xffffffffu, v.y, 0);
+    v.z = __shfl_sync(0xffffffffu, v.z, 0);
+    v.w = __shfl_sync(0xffffffffu, v.w, 0);
+    return v;
+}
+
+// A piece of a bulk row [c0, c1) (pieces start at c0 + m kPiece) has left its
+// partial in slot `slot`; the last piece to finish sums the row's partials in
+// piece order into y (so the result does not depend on timing) and re-arms
+// the counter.  True in the warp that wrote y.
+template <typename T>
+__device__ __forceinline__ bool bulk_finish(typename V2<T>::t* y, const typename V2<T>::t* P, int Pld, int* cnt, int c0, int c1, int slot,
+                                            int c, int ro, int lane)
+{
+    using C = typename V2<T>::t;
+    const int np = (c1 - c0 + kPiece - 1) / kPiece;
+    const int s0 = slot - (c - c0) / kPiece;
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atom_add_acq_rel(&cnt[c0], 1) + 1 == np;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return false;
+    __syncwarp();
+    for (int i = lane; i < ro; i += 32) {
+        T sr = 0, si = 0;
+        for (int q = 0; q < np; q++) {
+            const C p = __ldcg(&P[(size_t)(s0 + q) * Pld + i]);
+            sr += p.x;
+            si += p.y;
+        }
+        C o;
+        o.x = sr;
+        o.y = si;
+        y[i] = o;
+    }
+    if (lane == 0) cnt[c0] = 0;
+    return true;
+}
+
+// Every tree pass of one application.  Two lists of chunks: the chain (the
+// passes without slack, in phases, each warp with a static share of every
+// phase) and the bulk (the M2L levels with slack, cut into pieces of
+// kPiece chunks that warps take in order from a counter).  At the end of a
+// unit (a chain share or a piece) a warp takes the next chain share when the
+// passes it reads are complete, else the next piece when its inputs are
+// complete, else whichever reads the earlier phase; so bulk streams while the
+// chain waits on its short dependent steps.  The choice is made two chunks
+// ahead, so every chunk's matrix is copied in (TMA, two stages) before it is
+// needed.  Readiness is polled with relaxed loads issued an iteration early;
+// the first chunk of a pass waits (bounded) on its inputs' row counters with
+// acquire semantics.  Split chain rows are summed by the warp that holds
+// their first chunk, split bulk rows by their last piece, both in a fixed
+// order.  Every finished row moves its pass's counter.  Launched
+// cooperatively, so every warp is resident; a warp blocks only on rows of
+// earlier phases, or on bulk inputs when it has no chain work left, so the
+// waits end.
 template <typename T>
 __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* __restrict__ recs, const __grid_constant__ GroupArgs<T> g,
                                                                    const __grid_constant__ Sched sc, typename V2<T>::t* __restrict__ P,
@@ -565,14 +633,75 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
     C* xs = (C*)(wb + 2 * Cfg::kStage);
     unsigned long long* bar = (unsigned long long*)(wb + 2 * Cfg::kStage + Cfg::kXs);
     const int wg = blockIdx.x * kStreamWarps + warp;
-    Slice cur, n1, n2;
-    if (!slice_from(sc, 0, wg, cur)) return;
-    n1 = cur;
-    bool h1 = slice_next(sc, wg, n1), h2 = false;
-    if (h1) {
-        n2 = n1;
-        h2 = slice_next(sc, wg, n2);
+
+    // ---- scheduler (warp-uniform, except the lane-0 prefetches) ----
+    Slice cs;
+    bool hc = slice_from(sc, 0, wg, cs);  // a chain share is left
+    bool in_share = false;                // scheduling inside the share cs
+    int4 pc = make_int4(0, 0, 0, 0);      // piece being scheduled: {next chunk, end, slot, pass}
+    int4 pq = make_int4(0, 0, 0, -1);     // lane 0: the next piece (pass -1: none left)
+    int nid = 0;                          // lane 0: id of the piece after it
+    unsigned ready = 0, seen = 0;         // passes known complete (acquired / polled)
+    if (lane == 0 && sc.npieces > 0) {
+        const int id0 = atomicAdd(sc.next_piece, 1);
+        nid = atomicAdd(sc.next_piece, 1);
+        if (id0 < sc.npieces) pq = sc.pieces[id0];
     }
+    auto pick = [&]() {
+        Item r;
+        r.c = -1;
+        r.kind = 0;
+        r.aux = 0;
+        r.end = 0;
+        if (!in_share && pc.x >= pc.y) {
+            const int4 e = shfl4(pq);
+            const bool hb = e.w >= 0;
+            if (!hc && !hb) return r;
+            bool chain;
+            if (!hc)
+                chain = false;
+            else if (!hb)
+                chain = true;
+            else if ((sc.phdeps[cs.k] & ~(ready | seen)) == 0)
+                chain = true;
+            else if ((sc.deps[e.w] & ~(ready | seen)) == 0)
+                chain = false;
+            else
+                chain = !(sc.dphase[e.w] < cs.k - 1);
+            if (chain) {
+                in_share = true;
+            } else {
+                pc = e;
+                if (lane == 0) {
+                    pq = nid < sc.npieces ? sc.pieces[nid] : make_int4(0, 0, 0, -1);
+                    nid = atomicAdd(sc.next_piece, 1);
+                }
+            }
+        }
+        if (in_share) {
+            r.c = cs.c;
+            r.kind = 0;
+            r.aux = cs.k;
+            r.end = cs.e;
+            if (cs.c + 1 < cs.e) {
+                cs.c++;
+            } else {
+                in_share = false;
+                hc = slice_from(sc, cs.k + 1, wg, cs);
+            }
+        } else {
+            r.c = pc.x;
+            r.kind = 1;
+            r.aux = pc.z;
+            r.end = pc.y;
+            pc.x++;
+        }
+        return r;
+    };
+    Item cur = pick();
+    if (cur.c < 0) return;
+    Item n1 = pick();
+    Item n2 = n1.c >= 0 ? pick() : Item{-1, 0, 0, 0};
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -580,7 +709,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
         unsigned bytes;
         const char* src = chunk_src<T>(g, recs[2 * cur.c], recs[2 * cur.c + 1], bytes);
         tma_load(stage(0), src, bytes, &bar[0]);
-        if (h1) {
+        if (n1.c >= 0) {
             src = chunk_src<T>(g, recs[2 * n1.c], recs[2 * n1.c + 1], bytes);
             tma_load(stage(1), src, bytes, &bar[1]);
         }
@@ -593,12 +722,11 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
     int4 na = make_int4(-1, -1, 0, 0), nb = make_int4(0, 0, 0, 0);
     int xc[kMaxPrefetch], xi[kMaxPrefetch];  // input indices of the current and the next chunk
     gather_idx<T>(g, ra, lane, xc);
-    if (h1) {
+    if (n1.c >= 0) {
         na = recs[2 * n1.c];
         nb = recs[2 * n1.c + 1];
         gather_idx<T>(g, na, lane, xi);
     }
-    unsigned ready = 0;
     bool have_x = false;
     C xr[kMaxPrefetch];
     Acc<T> acc;
@@ -606,6 +734,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
     for (int it = 0;; it++) {
         const int s = it & 1;
         const unsigned parity = (unsigned)((it >> 1) & 1);
+        const bool h1 = n1.c >= 0, h2 = n2.c >= 0;
         // a wait that gives up: flag it, let this warp's copies in flight land, leave
         auto bail = [&]() {
             if (lane == 0) {
@@ -622,6 +751,24 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
                 return;
             }
             gather_val<T>(g, ra, lane, xc, xr);
+        }
+        // readiness polls for the next choice (lane 0; consumed after this chunk)
+        int q1 = -1, q2 = -1, v1 = 0, v2 = 0;
+        if (lane == 0) {
+            if (hc && !in_share) {
+                const unsigned m = sc.phdeps[cs.k] & ~(ready | seen);
+                if (m) {
+                    q1 = __ffs(m) - 1;
+                    v1 = ld_relaxed(&done[q1 * kDoneStride]);
+                }
+            }
+            if (pc.x >= pc.y && pq.w >= 0) {
+                const unsigned m = sc.deps[pq.w] & ~(ready | seen);
+                if (m) {
+                    q2 = __ffs(m) - 1;
+                    v2 = ld_relaxed(&done[q2 * kDoneStride]);
+                }
+            }
         }
         // commit this chunk's inputs
         const int ncol = ra.z;
@@ -664,39 +811,56 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
             for (int k = 0; k < kMaxPrefetch; k++) xc[k] = xi[k];  // the next chunk gathers at the top
         }
         if (h2) gather_idx<T>(g, fa, lane, xi);
-        // end of this row's run in the share: write it out
-        const bool row_ends = !h1 || na.x != ra.x || na.y != ra.y;
+        // end of this row's run in the unit: write it out
+        const bool row_ends = !h1 || n1.kind != cur.kind || n1.aux != cur.aux || na.x != ra.x || na.y != ra.y;
         if (row_ends) {
             C* yrow = pa.y + (size_t)ra.y * pa.ldy;
-            if (rb.w < cur.b) {
-                // the row began in an earlier share: leave a partial for its owner
-                flush_row<T>(acc, ro, lane, P + (size_t)share_slot(sc, cur.k, cur.b) * Pld, false, 0);
-                put_partial(cnt, rb.w, lane);
-            } else {
-                flush_row<T>(acc, ro, lane, yrow, true, 0);
-                if (rb.z > cur.e && !own_row<T>(yrow, P, Pld, cnt, rb.w, rb.z, sc, cur.k, ro, lane)) {
-                    // the copies in flight now: the next chunk's (other stage), the one after (this stage)
-                    if (lane == 0) {
-                        atomicExch(err, 1);
-                        if (h1) mbar_wait(&bar[s ^ 1], ((it + 1) >> 1) & 1);
-                        if (h2) mbar_wait(&bar[s], ((it + 2) >> 1) & 1);
+            bool fin = true;
+            if (cur.kind == 0) {
+                const int b = sc.base[cur.aux] + wg * sc.kpw[cur.aux];
+                if (rb.w < b) {
+                    // the row began in an earlier share: leave a partial for its owner
+                    flush_row<T>(acc, ro, lane, P + (size_t)share_slot(sc, cur.aux, b) * Pld, false, 0);
+                    put_partial(cnt, rb.w, lane);
+                    fin = false;
+                } else {
+                    flush_row<T>(acc, ro, lane, yrow, true, 0);
+                    if (rb.z > cur.end && !own_row<T>(yrow, P, Pld, cnt, rb.w, rb.z, sc, cur.aux, ro, lane)) {
+                        // the copies in flight now: the next chunk's (other stage), the one after (this stage)
+                        if (lane == 0) {
+                            atomicExch(err, 1);
+                            if (h1) mbar_wait(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+                            if (h2) mbar_wait(&bar[s], ((it + 2) >> 1) & 1);
+                        }
+                        __syncwarp();
+                        return;
                     }
-                    __syncwarp();
-                    return;
                 }
-                row_done(done, pass, lane);
+            } else if (rb.z - rb.w <= kPiece) {
+                flush_row<T>(acc, ro, lane, yrow, true, 0);  // the piece is the whole row
+            } else {
+                flush_row<T>(acc, ro, lane, P + (size_t)cur.aux * Pld, false, 0);
+                fin = bulk_finish<T>(yrow, P, Pld, cnt, rb.w, rb.z, cur.aux, cur.c, ro, lane);
             }
+            if (fin) row_done(done, pass, lane);
             acc.zero();
         }
         if (!h1) break;
+        // fold in the polls, then choose the chunk after next
+        unsigned add = 0;
+        if (lane == 0) {
+            if (q1 >= 0 && v1 >= sc.target[q1]) add |= 1u << q1;
+            if (q2 >= 0 && v2 >= sc.target[q2]) add |= 1u << q2;
+        }
+        seen |= __shfl_sync(0xffffffffu, add, 0);
+        const Item n3 = h2 ? pick() : Item{-1, 0, 0, 0};
         cur = n1;
         ra = na;
         rb = nb;
         n1 = n2;
         na = fa;
         nb = fb;
-        h1 = h2;
-        if (h2) h2 = slice_next(sc, wg, n2);
+        n2 = n3;
     }
 }
 
@@ -921,8 +1085,8 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
 // Morton order (a 2 x 2 quad); the inputs of the 4 x 4 leaves around it are
 // read in complex128, rounded to T once and kept in shared memory (FP64
 // conversions are scarce on this GPU).  The leaves' locals are lc (+ lc2 when
-// not null).  done (not null): row counters of the fused launch before,
-// reset here for the next application.
+// not null).  done (not null): row and piece counters of the fused launch
+// before, reset here for the next application.
 constexpr int kLeafPerCta = 4;
 
 template <typename T>
@@ -934,14 +1098,14 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
                                                                       const typename V2<T>::t* __restrict__ lc,
                                                                       const typename V2<T>::t* __restrict__ lc2,
                                                                       const double2* __restrict__ v, const double* __restrict__ q, double k2,
-                                                                      double2* __restrict__ out, int* __restrict__ done, int npass)
+                                                                      double2* __restrict__ out, int* __restrict__ done)
 {
     using C = typename V2<T>::t;
     static_assert(kLeafPerCta == 4, "a CTA takes one 2 x 2 quad of leaves (four consecutive Morton indices)");
     __shared__ __align__(16) C sn[9 * 256];
     __shared__ __align__(16) C vq[16][16];  // inputs of the 4 x 4 leaves around the quad, rounded to T once
     __shared__ C part[2][kLeafPerCta * 16];
-    if (done != nullptr && blockIdx.x == 0 && threadIdx.x < npass) done[threadIdx.x * kDoneStride] = 0;
+    if (done != nullptr && blockIdx.x == 0 && threadIdx.x <= kMaxPass) done[threadIdx.x * kDoneStride] = 0;
     auto rnd = [](double2 d) {
         C c;
         c.x = (T)d.x;
@@ -1227,9 +1391,9 @@ int fused_ctas()
     return std::max(1, sms * std::max(per_sm, 1));
 }
 
-// Warp shares of the fused list for a grid of `warps` warps: chunks per warp
-// in each phase, and the shares in the phases before.  Returns the shares.
-int fused_shares(const Fused& F, int warps, int* kpw, int* sbase)
+// Warp shares of a plan's chain list for a grid of `warps` warps: chunks per
+// warp in each phase, and the shares in the phases before.  Returns the shares.
+int fused_shares(const FusedPlan& F, int warps, int* kpw, int* sbase)
 {
     int n = 0;
     for (int k = 0; k < F.nph; k++) {
@@ -1245,12 +1409,12 @@ int fused_shares(const Fused& F, int warps, int* kpw, int* sbase)
 // pass comes after those it reads: up at levels L..top, M2L at top..L, down
 // at top..L-1 (the down pass of level nu reads the M2L locals and the
 // parent's down output of level nu and writes its own buffer for level nu+1).
-// Phases: a pass without slack (the dependent chain) sits at its earliest
-// phase, one more than the latest of the passes it reads; the rows of a pass
-// with slack (an M2L whose readers come later) go into the phases of its
-// window (see below).  Every row a chunk reads lies in an earlier phase, and
-// a warp works through its shares phase by phase, so the waits cannot form a
-// cycle.
+// A pass's earliest phase (asap) is one more than the latest of the passes it
+// reads, its latest (alap) one less than the earliest of its readers; passes
+// with alap > asap (M2L below the top level) have slack, and every pass they
+// read is on the chain.  Every row a chunk reads lies in an earlier phase (or
+// in a bulk pass whose inputs do), and a warp works through its shares phase
+// by phase, so the waits cannot form a cycle.
 void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
 {
     Fused& F = d.fz;
@@ -1289,7 +1453,6 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
         cuts.push_back(cut_pass(*hs[p], p, ldx[p], 0, nullptr));
         pld = std::max(pld, cuts[p].pld);
     }
-    // earliest (asap) and latest (alap) phase of every pass
     std::vector<int> asap(np, 0), alap(np, 0);
     for (int p = 0; p < np; p++)
         for (int q = 0; q < p; q++)
@@ -1297,53 +1460,97 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
     int nph = 0;
     for (int p = 0; p < np; p++) nph = std::max(nph, asap[p] + 1);
     if (nph > kMaxPhase) fail(DAFMM_EBADARG, "too many phases for the fused launch");
-    // latest: before the earliest phase of every reader, so that each row a
-    // chunk reads lies in an earlier phase wherever the reader's rows go
     for (int p = 0; p < np; p++) {
         alap[p] = nph - 1;
         for (int r = p + 1; r < np; r++)
             if (deps[r] >> p & 1u) alap[p] = std::min(alap[p], asap[r] - 1);
     }
-    // place rows: the list of (pass, row) of every phase.  Chain phases get
-    // about one chunk per warp of slack rows (more would take bandwidth from
-    // the chain); the rest of every slack pass goes to the earliest deadline
-    // among them, where one long phase streams it at full bandwidth.
-    const int warps32 = F.ctas[1] * kStreamWarps;
-    const long fill = warps32;
-    int bulk_at = nph - 1;
+    auto chunks = [&](int p, int r) { return cuts[p].first[r + 1] - cuts[p].first[r]; };
+    std::vector<char> slack(np, 0);
+    for (int p = 0; p < np; p++) slack[p] = alap[p] > asap[p];
+    F.dphase.assign(np, -1);
     for (int p = 0; p < np; p++)
-        if (alap[p] > asap[p]) bulk_at = std::min(bulk_at, alap[p]);
-    std::vector<std::vector<std::pair<int, int>>> rows(nph);
-    std::vector<long> load(nph, 0);
-    auto chunks = [&](int p, int r) { return (long)(cuts[p].first[r + 1] - cuts[p].first[r]); };
-    for (int p = 0; p < np; p++)
-        if (alap[p] == asap[p])
-            for (int r = 0; r < hs[p]->nrows; r++)
-                if (chunks(p, r)) {
-                    rows[asap[p]].push_back({p, r});
-                    load[asap[p]] += chunks(p, r);
-                }
-    std::vector<int> next(np, 0);  // next unplaced row of a pass with slack
-    for (int k = 0; k < nph; k++) {
-        std::vector<int> cand;
-        for (int p = 0; p < np; p++)
-            if (alap[p] > asap[p] && asap[p] <= k && k <= alap[p]) cand.push_back(p);
-        std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return alap[a] < alap[b]; });
-        for (int p : cand)
-            for (; next[p] < hs[p]->nrows && (load[k] < fill || k == std::min(alap[p], std::max(asap[p], bulk_at))); next[p]++) {
-                if (!chunks(p, next[p])) continue;
-                rows[k].push_back({p, next[p]});
-                load[k] += chunks(p, next[p]);
+        for (int q = 0; q < np; q++)
+            if (deps[p] >> q & 1u) {
+                if (slack[p] && slack[q]) fail(DAFMM_EBADARG, "fused launch: a pass with slack reads another");
+                F.dphase[p] = std::max(F.dphase[p], asap[q]);
             }
+    F.g.Pld = std::max(pld, 1);
+    for (int k = 0; k < 2; k++) {
+        FusedPlan& P = F.plan[k];
+        const bool dynamic = k == 0;
+        // rows of every phase: the chain at its phase; in the static plan the
+        // slack rows fill each phase up to about one chunk per warp (more would
+        // take bandwidth from the chain), the rest going to the earliest
+        // deadline among them, where one long phase streams it
+        std::vector<std::vector<std::pair<int, int>>> rows(nph);
+        std::vector<long> load(nph, 0);
+        for (int p = 0; p < np; p++)
+            if (!slack[p])
+                for (int r = 0; r < hs[p]->nrows; r++)
+                    if (chunks(p, r)) {
+                        rows[asap[p]].push_back({p, r});
+                        load[asap[p]] += chunks(p, r);
+                    }
+        if (!dynamic) {
+            const long fill = (long)F.ctas[k] * kStreamWarps;
+            int bulk_at = nph - 1;
+            for (int p = 0; p < np; p++)
+                if (slack[p]) bulk_at = std::min(bulk_at, alap[p]);
+            std::vector<int> next(np, 0);
+            for (int ph = 0; ph < nph; ph++) {
+                std::vector<int> cand;
+                for (int p = 0; p < np; p++)
+                    if (slack[p] && asap[p] <= ph && ph <= alap[p]) cand.push_back(p);
+                std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return alap[a] < alap[b]; });
+                for (int p : cand)
+                    for (; next[p] < hs[p]->nrows && (load[ph] < fill || ph == std::min(alap[p], std::max(asap[p], bulk_at)));
+                         next[p]++) {
+                        if (!chunks(p, next[p])) continue;
+                        rows[ph].push_back({p, next[p]});
+                        load[ph] += chunks(p, next[p]);
+                    }
+            }
+        }
+        std::vector<int4> recs;
+        P.nph = nph;
+        P.base.assign(nph + 1, 0);
+        P.phdeps.assign(nph, 0u);
+        for (int ph = 0; ph < nph; ph++) {
+            P.base[ph] = (int)(recs.size() / 2);
+            for (auto& pr : rows[ph]) {
+                P.phdeps[ph] |= deps[pr.first];
+                place_row(recs, cuts[pr.first], pr.second);
+            }
+        }
+        P.base[nph] = (int)(recs.size() / 2);
+        int kpw[kMaxPhase], sbase[kMaxPhase];
+        const int chain_slots = fused_shares(P, F.ctas[k] * kStreamWarps, kpw, sbase);
+        // dynamic plan: the slack passes as pieces of kPiece chunks, earliest inputs first
+        std::vector<int4> pieces;
+        if (dynamic) {
+            std::vector<int> order;
+            for (int p = 0; p < np; p++)
+                if (slack[p]) order.push_back(p);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return asap[a] < asap[b]; });
+            for (int p : order)
+                for (int r = 0; r < hs[p]->nrows; r++) {
+                    const int n = chunks(p, r);
+                    if (!n) continue;
+                    const int c0 = (int)(recs.size() / 2);
+                    place_row(recs, cuts[p], r);
+                    for (int j = 0; j < n; j += kPiece)
+                        pieces.push_back(make_int4(c0 + j, c0 + std::min(n, j + kPiece), chain_slots + (int)pieces.size(), p));
+                }
+        }
+        P.npieces = (int)pieces.size();
+        if (!pieces.empty()) upload_vec(pieces, &P.pieces);
+        P.nch = (int)(recs.size() / 2);
+        upload_vec(recs, &P.chunks);
+        std::vector<int> zeros(std::max(P.nch, 1), 0);
+        upload_vec(zeros, &P.cnt);
+        P.part = (size_t)(chain_slots + P.npieces) * F.g.Pld;
     }
-    std::vector<int4> recs;
-    F.base.assign(nph + 1, 0);
-    for (int k = 0; k < nph; k++) {
-        F.base[k] = (int)(recs.size() / 2);
-        for (auto& pr : rows[k]) place_row(recs, cuts[pr.first], pr.second);
-    }
-    F.base[nph] = (int)(recs.size() / 2);
-    F.nph = nph;
     F.deps = deps;
     F.target.assign(np, 0);
     for (int p = 0; p < np; p++)
@@ -1351,15 +1558,17 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
     F.g.passes = passes;
     F.g.accumulate = 0;
     for (int p = 0; p < np; p++) upload_tables(F.g, cuts[p]);
-    finish_group(F.g, recs, pld);
-    std::vector<int> zeros(kMaxPass * kDoneStride, 0);
+    std::vector<int> zeros((kMaxPass + 1) * kDoneStride, 0);
     upload_vec(zeros, &F.done);
 }
 
 void free_fused(Fused& F)
 {
-    cudaFree(F.g.chunks);
-    cudaFree(F.g.cnt);
+    for (FusedPlan& P : F.plan) {
+        cudaFree(P.pieces);
+        cudaFree(P.chunks);
+        cudaFree(P.cnt);
+    }
     for (long* p : F.g.rbase) cudaFree(p);
     for (int* p : F.g.cbase) cudaFree(p);
     for (int* p : F.g.xmap) cudaFree(p);
@@ -1469,20 +1678,27 @@ template <typename T>
 void launch_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const double* v, cudaStream_t s)
 {
     const Fused& F = d.fz;
-    if (F.g.nch == 0) return;
+    const int k = sizeof(T) == 4 ? 1 : 0;
+    const FusedPlan& FP = F.plan[k];
+    if (FP.nch == 0) return;
     GroupArgs<T> ga;
     std::memset(&ga, 0, sizeof(ga));
     for (size_t p = 0; p < F.g.passes.size(); p++) ga.p[p] = fused_pass_args<T>(t, d, b, v, (int)p);
-    const int ctas = F.ctas[sizeof(T) == 4];
+    const int ctas = F.ctas[k];
     const int warps = ctas * kStreamWarps;
     Sched sc;
     std::memset(&sc, 0, sizeof(sc));
-    sc.nph = F.nph;
-    for (int k = 0; k <= F.nph; k++) sc.base[k] = F.base[k];
-    fused_shares(F, warps, sc.kpw, sc.sbase);
+    sc.nph = FP.nph;
+    for (int ph = 0; ph <= FP.nph; ph++) sc.base[ph] = FP.base[ph];
+    fused_shares(FP, warps, sc.kpw, sc.sbase);
+    for (int ph = 0; ph < FP.nph; ph++) sc.phdeps[ph] = FP.phdeps[ph];
+    sc.npieces = FP.npieces;
+    sc.pieces = FP.pieces;
+    sc.next_piece = F.done + kMaxPass * kDoneStride;
     for (size_t p = 0; p < F.g.passes.size(); p++) {
         sc.deps[p] = F.deps[p];
         sc.target[p] = F.target[p];
+        sc.dphase[p] = F.dphase[p];
     }
     if (d.stall_pass >= 0) sc.target[d.stall_pass] += 1;  // a row nobody writes: the waits on it give up
     cudaLaunchConfig_t cfg;
@@ -1496,7 +1712,7 @@ void launch_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const doubl
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, stream_kernel<T>, (const int4*)F.g.chunks, ga, sc, b.part, F.g.Pld, F.g.cnt, F.done, d.err));
+    CK(cudaLaunchKernelEx(&cfg, stream_kernel<T>, (const int4*)FP.chunks, ga, sc, b.part, F.g.Pld, FP.cnt, F.done, d.err));
 }
 
 // Events recorded while a graph is being captured (its five pass marks).
@@ -1553,7 +1769,7 @@ void run_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const double* 
         nleaf, d.nbr, nearp, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
         l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
         far && L > t.top ? b.lcd[L] : nullptr, (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out,
-        far ? d.fz.done : nullptr, (int)d.fz.g.passes.size());
+        far ? d.fz.done : nullptr);
     CK(cudaGetLastError());
     mark(prof, 4, s);
 }
@@ -1643,12 +1859,7 @@ void run_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, 
 
 size_t max_group_part(const OpsDev& d)
 {
-    size_t m = (size_t)d.m2l.nch * d.m2l.Pld;
-    for (int k = 0; k < 2; k++) {
-        int kpw[kMaxPhase], sbase[kMaxPhase];
-        const int shares = fused_shares(d.fz, d.fz.ctas[k] * kStreamWarps, kpw, sbase);
-        m = std::max(m, (size_t)shares * d.fz.g.Pld);
-    }
+    size_t m = std::max({(size_t)d.m2l.nch * d.m2l.Pld, d.fz.plan[0].part, d.fz.plan[1].part});
     for (const Group& g : d.up) m = std::max(m, (size_t)g.nch * g.Pld);
     for (const Group& g : d.down) m = std::max(m, (size_t)g.nch * g.Pld);
     return m;
@@ -1856,8 +2067,9 @@ int sync_and_check(OpsDev& d, cudaStream_t stream)
         for (auto& g : d.up) rearm(g);
         for (auto& g : d.down) rearm(g);
         rearm(d.m2l);
-        rearm(d.fz.g);
-        if (d.fz.done) CK(cudaMemset(d.fz.done, 0, sizeof(int) * kMaxPass * kDoneStride));
+        for (FusedPlan& P : d.fz.plan)
+            if (P.cnt) CK(cudaMemset(P.cnt, 0, sizeof(int) * std::max(P.nch, 1)));
+        if (d.fz.done) CK(cudaMemset(d.fz.done, 0, sizeof(int) * (kMaxPass + 1) * kDoneStride));
         CK(cudaMemset(d.err, 0, sizeof(int)));
         return DAFMM_ETIMEOUT;
     }
@@ -1866,8 +2078,7 @@ int sync_and_check(OpsDev& d, cudaStream_t stream)
 
 int launches_per_call(const Tree& t, const OpsDev& d, int precision)
 {
-    (void)precision;  // the complex64 rounding happens inside the kernels
-    return 1 + (t.top <= t.L && d.fz.g.nch > 0 ? 1 : 0);  // fused far field, leaf kernel
+    return 1 + (t.top <= t.L && d.fz.plan[precision == DAFMM_FP64 ? 0 : 1].nch > 0 ? 1 : 0);  // fused far field, leaf kernel
 }
 
 namespace {

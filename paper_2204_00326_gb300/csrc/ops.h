@@ -51,17 +51,33 @@ struct Group {
 };
 
 // Every tree pass of a single-right-hand-side application in one cooperative
-// launch.  Chunks are ordered by phase; a warp takes an equal share of every
-// phase in turn, and before the first chunk of a pass it waits until the
-// passes it reads have written all their rows (per-pass row counters).
-struct Fused {
-    Group g;                      // passes, chunks (phase by phase), partial counters
-    std::vector<unsigned> deps;   // per pass: bit mask of the passes whose output it reads
-    std::vector<int> target;      // per pass: rows it writes
-    std::vector<int> base;        // per phase: first chunk; base[nph] = chunks
+// launch.  The passes on the dependent chain are ordered by phase and every
+// warp takes a fixed share of each phase.  The passes with slack either sit
+// in the phases too (complex64: bandwidth-bound, they stream in one long
+// phase) or are cut into pieces that warps take from a counter while the
+// chain waits (complex128: arithmetic-bound, they fill the chain's latency).
+// Before the first chunk of a pass a warp waits until the passes it reads
+// have written all their rows (per-pass row counters).
+struct FusedPlan {
+    int4* chunks = nullptr;        // the chain list (phase by phase), then the bulk list
+    int* cnt = nullptr;            // per chunk: counter of a split row starting there
+    int nch = 0;
     int nph = 0;
-    int ctas[2] = {0, 0};         // persistent grid, [0] complex128, [1] complex64
-    int* done = nullptr;          // per pass: rows written in the running application
+    std::vector<int> base;         // per chain phase: first chunk; base[nph] = chain chunks
+    std::vector<unsigned> phdeps;  // per chain phase: passes read by its passes
+    int npieces = 0;               // bulk pieces (chunk ranges of one row), taken in order
+    int4* pieces = nullptr;        // per piece: {first chunk, end chunk, partial slot, pass}
+    size_t part = 0;               // complex elements of chunk partials it uses
+};
+
+struct Fused {
+    Group g;                       // passes and their tables (g.chunks unused)
+    std::vector<unsigned> deps;    // per pass: bit mask of the passes whose output it reads
+    std::vector<int> target;       // per pass: rows it writes
+    std::vector<int> dphase;       // per pass: latest phase among the passes it reads (-1: none)
+    FusedPlan plan[2];             // [0] complex128, [1] complex64
+    int ctas[2] = {0, 0};          // persistent grid, [0] complex128, [1] complex64
+    int* done = nullptr;           // per pass: rows written in the running application; then the piece counter
 };
 
 // One captured application (per precision), replayed while the vector

@@ -50,6 +50,13 @@ def _args():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-residual solves")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides of the batched measurement (1 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--learned", action="store_true",
+                    help="instead of the matvec line: train the initial-guess network and compare solves from its guess "
+                         "and from zero on --workload (default grid512_k160_bumps8)")
+    ap.add_argument("--learned-train", type=int, default=2000, help="training problems (solved at 64 x 64)")
+    ap.add_argument("--learned-steps", type=int, default=6000, help="Adam steps")
+    ap.add_argument("--learned-base", type=int, default=32)
+    ap.add_argument("--learned-levels", type=int, default=4)
     return ap.parse_args()
 
 
@@ -192,11 +199,82 @@ def run_reference(a, w):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(a):
+    """Learned initial guess on the target workload: train at 64 x 64 with the
+    same points per wavelength, then HODLR-preconditioned GMRES (mixed
+    precision, FP64 residual) to 1e-8 from zero and from the guess."""
+    import torch
+
+    import paper_2204_00326_gb300 as pkg
+
+    pkg.build()
+    from paper_2204_00326_gb300 import learned as Lr
+    from paper_2204_00326_gb300 import native as N
+    from paper_2204_00326_gb300.operator import DafmmOperator
+
+    name = a.workload if "--workload" in sys.argv else W.GRID512_K160.name
+    w = W.WORKLOADS[name]
+    n_t = 64
+    k_t = w.kappa * n_t / w.n_side
+    X, Y, t_gen = Lr.generate(n_t, k_t, count=a.learned_train, seed=100000)
+    net = N.unet_create(levels=a.learned_levels, base=a.learned_base, seed=1)
+    losses, t_train = Lr.train(net, X, Y, steps=a.learned_steps, batch=16, lr=1e-3, lr_final=5e-5)
+    del X, Y
+    result = {"mode": "learned_guess", "workload": w.name, "n_side": w.n_side, "N": w.N, "kappa": w.kappa,
+              "train": {"grid": n_t, "kappa": k_t, "problems": a.learned_train, "steps": a.learned_steps, "batch": 16,
+                        "levels": a.learned_levels, "base": a.learned_base, "params": N.unet_num_params(net),
+                        "solve_seconds": t_gen, "train_seconds": t_train,
+                        "loss_first": float(np.mean(losses[:50])), "loss_last": float(np.mean(losses[-50:]))}}
+    # in-distribution check at the training size
+    op_t = DafmmOperator(n_t, k_t, np.zeros(n_t * n_t))
+    q, f = Lr.problem(op_t.xy, k_t, 8, seed=999999)
+    N.dafmm_set_contrast(op_t.ops, torch.as_tensor(q, device="cuda"))
+    M = N.hodlr_factor(op_t.ops, rank=15, leaf_size=64)
+    result["train_size"] = Lr.compare(op_t, net, f, M)
+    N.hodlr_destroy(M)
+    op_t.close()
+    # the target workload
+    t0 = time.perf_counter()
+    op = DafmmOperator(w.n_side, w.kappa, lambda xy: W.contrast(w, xy))
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M = N.hodlr_factor(op.ops, rank=15, leaf_size=64)
+    t_factor = time.perf_counter() - t0
+    f = -w.kappa ** 2 * op.q * W.plane_waves(w.kappa, op.xy)[:, 0]
+    Lr.compare(op, net, f, M)  # warm-up (graph capture, workspaces)
+    result["target"] = Lr.compare(op, net, f, M)
+    result["target"]["setup_seconds"] = setup
+    result["target"]["hodlr_factor_seconds"] = t_factor
+    # network inference on the target grid
+    fd = torch.as_tensor(f, device="cuda")
+    xg = torch.empty_like(fd)
+    for _ in range(3):
+        N.unet_guess(net, op.ops, fd, xg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        N.unet_guess(net, op.ops, fd, xg)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    flops = Lr.forward_flops(a.learned_levels, a.learned_base, w.n_side, w.n_side)
+    result["inference"] = {"ms": ms, "gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
+                           "peak_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "peak_kind": "FP32 FMA lanes x clock (CUDA cores)"}
+    N.hodlr_destroy(M)
+    op.close()
+    N.unet_destroy(net)
+    print(json.dumps(result), flush=True)
+
+
 def main():
     a = _args()
     w = W.WORKLOADS[a.workload]
     if a.impl == "reference":
         run_reference(a, w)
+        return
+    if a.learned:
+        run_learned(a)
         return
     rank, world, local = _dist_env()
     import torch

@@ -316,6 +316,16 @@ int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v_dev, double* out_
 int dafmm_sync(dafmm_ops* ops, void* stream);
 
 /*
+ * dafmm_set_contrast -- replace the contrast q of an operator (N doubles on
+ * the device, copied on `stream`).  The NCA compresses K, which does not
+ * depend on q (q enters A = I + kappa^2 diag(q) K only in the epilogue), so
+ * one tree and one set of operators serve any number of contrasts.  A HODLR
+ * preconditioner factored earlier keeps the q it was built with.  Errors:
+ * DAFMM_EBADARG for NULL arguments, DAFMM_ECUDA.
+ */
+int dafmm_set_contrast(dafmm_ops* ops, const double* q_dev, void* stream);
+
+/*
  * dafmm_debug_stall -- test support for the timeout path (the paper has no
  * counterpart).  The next single-right-hand-side dafmm_matvec on this handle
  * runs without graph replay and its kernel waits for one more row of tree
@@ -349,6 +359,91 @@ int dafmm_profile_read(dafmm_ops* ops, dafmm_profile_t* out);
 
 /* Release an operator and its device memory.  NULL is accepted. */
 int ops_destroy(dafmm_ops* ops);
+
+/* ------------------------------------------------------------------------
+ * Learned initial guess and coarse correction.  Not part of the paper: a
+ * convolutional U-Net maps (q, f) on the node grid to an approximation of
+ * the solution psi of Eq. 13, trained on the library's own solutions.  The
+ * node grid is the n_side x n_side image whose pixel (x, y) holds node
+ * (4 lx + k1, 4 ly + k2) of leaf (lx, ly) (Morton order) at local index
+ * k1 + 4 k2.
+ * Network: `levels` resolution levels with base * 2^l channels at level l;
+ * per level two 3x3 convolutions (bias, ReLU), 2 x 2 average pooling
+ * between levels, nearest 2x upsampling, a 3x3 up-convolution, the
+ * concatenation [skip, up] and two 3x3 convolutions on the way up, a final
+ * 1x1 convolution.  Zero padding.  Activations and weights are rounded to
+ * BF16 for the products, sums are FP32; FP32 master weights, Adam.
+ * Parameters, flattened: for every convolution in the order (encoder level
+ * 0..levels-1: first, second), (decoder level levels-2..0: up, first,
+ * second), (output), the weights [ky][kx][c_in][c_out] then the bias
+ * [c_out].
+ * ------------------------------------------------------------------------ */
+typedef struct unet_params {
+    int levels;               /* 1..6 (4 is typical) */
+    int base;                 /* channels at full resolution, 1..256 (32 is typical) */
+    int in_ch;                /* 3: q, Re f / s, Im f / s */
+    int out_ch;               /* 2: Re psi / s, Im psi / s */
+    unsigned long long seed;  /* He-normal weight initialisation (SplitMix64, Box-Muller) */
+    int reserved[8];          /* must be zero */
+} unet_params;
+
+typedef struct dafmm_unet dafmm_unet;
+
+/* Create a network with freshly initialised weights.  DAFMM_EBADARG for
+ * parameters outside the ranges above, DAFMM_ENOMEM, DAFMM_ECUDA. */
+int unet_create(const unet_params* p, dafmm_unet** out);
+int unet_destroy(dafmm_unet* net);
+/* Number of FP32 parameters. */
+int unet_num_params(const dafmm_unet* net, long* n);
+/* Copy the FP32 parameters (layout above) to / from a host array. */
+int unet_get_params(const dafmm_unet* net, float* host);
+int unet_set_params(dafmm_unet* net, const float* host);
+
+/*
+ * unet_forward -- out = N(in) for `batch` images of height x width
+ * (multiples of 2^(levels-1)).  in_dev: [batch][height][width][in_ch] FP32,
+ * out_dev: [batch][height][width][out_ch] FP32, both device, caller-owned.
+ * Activations are kept in the handle (grown on demand; not thread-safe).
+ */
+int unet_forward(dafmm_unet* net, int batch, int height, int width, const float* in_dev, float* out_dev, void* stream);
+
+/*
+ * unet_backward -- forward, mean squared error against target_dev (same
+ * shape as out_dev), and the gradient of that error with respect to every
+ * parameter, kept in the handle (replacing the previous one).  out_dev
+ * receives the forward output; *loss_host the error.  Synchronises.
+ */
+int unet_backward(dafmm_unet* net, int batch, int height, int width, const float* in_dev, const float* target_dev, float* out_dev,
+                  double* loss_host, void* stream);
+/* The gradient of the last unet_backward (layout of the parameters). */
+int unet_get_grads(const dafmm_unet* net, float* host);
+/* One Adam step (Kingma and Ba, with bias correction) with that gradient. */
+int unet_adam(dafmm_unet* net, float lr, float beta1, float beta2, float eps, void* stream);
+
+/*
+ * unet_guess -- x = s N(q, f / s) on the operator's node grid, s = max |f|
+ * (q: the contrast the operator was built with).  f_dev, x_dev: N complex128.
+ */
+int unet_guess(dafmm_unet* net, const dafmm_ops* ops, const double* f_dev, double* x_dev, void* stream);
+
+/* What gmres_solve_learned adds to gmres_stats. */
+typedef struct learned_stats {
+    int guess_used;          /* 1: the network's guess was accepted as x0 */
+    double guess_residual;   /* |f - A x_guess| / |f| (FP64), or -1 when no guess was made */
+    int corrections;         /* applications of the learned coarse correction */
+} learned_stats;
+
+/*
+ * gmres_solve_learned -- gmres_solve with the network's help.  flags bit 0:
+ * start from x0 = unet_guess(f) when |f - A x0| < |f| (FP64 residual),
+ * else from the caller's x.  Bit 1: right preconditioner
+ * z = M^-1 r + alpha s N(q, r / s), s = max |r| (a nonlinear coarse
+ * correction added to the HODLR solve, or to the identity when M is NULL;
+ * flexible GMRES keeps the preconditioned vectors).  Otherwise as
+ * gmres_solve.
+ */
+int gmres_solve_learned(dafmm_ops* ops, const dafmm_hodlr* M, dafmm_unet* net, int flags, double alpha, const double* f_dev,
+                        double* x_dev, const gmres_opts* opts, gmres_stats* st, learned_stats* ls, void* stream);
 
 #ifdef __cplusplus
 }

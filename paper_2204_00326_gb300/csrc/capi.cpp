@@ -256,21 +256,57 @@ int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v, double* out, int
     });
 }
 
+namespace {
+void cuda_check(cudaError_t e, const char* what)
+{
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(DAFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+void check_gmres(const dafmm_ops* ops, const double* f, const double* x, const gmres_opts* opts, const gmres_stats* st)
+{
+    if (!ops || !f || !x || !opts || !st) fail(DAFMM_EBADARG, "NULL argument");
+    if (opts->restart < 1 || opts->restart > 128) fail(DAFMM_EBADARG, "restart must lie in 1..128");
+    if (opts->max_iters < 0) fail(DAFMM_EBADARG, "max_iters must be >= 0");
+    if (!(opts->tol > 0)) fail(DAFMM_EBADARG, "tol must be positive");
+    if (opts->precision != DAFMM_FP64 && opts->precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+    if (opts->precision == DAFMM_MIXED && !(opts->inner_tol > 0 && opts->inner_tol < 1))
+        fail(DAFMM_EBADARG, "inner_tol must lie in (0, 1) in mixed precision");
+    for (int v : opts->reserved)
+        if (v) fail(DAFMM_EBADARG, "reserved options must be zero");
+    if (f == x) fail(DAFMM_EBADARG, "f and x must not overlap");
+}
+
+// z = M^-1 v + alpha s N(q, v / s) (M^-1 = identity when M is NULL)
+struct LearnedPrec {
+    const dafmm_hodlr* M;
+    dafmm_unet* net;
+    const Tree* t;
+    const OpsDev* d;
+    double alpha;
+    int applies;
+};
+
+void learned_prec(const void* P, const double* v, double* z, int precision, cudaStream_t s)
+{
+    auto* lp = (LearnedPrec*)P;
+    if (lp->M)
+        hodlr_prec(lp->M, v, z, precision, s);
+    else
+        cuda_check(cudaMemcpyAsync(z, v, sizeof(double2) * lp->t->N, cudaMemcpyDeviceToDevice, s), "cudaMemcpyAsync");
+    unet_apply_nodes(lp->net, *lp->t, *lp->d, v, z, 1.0, lp->alpha, s);
+    lp->applies++;
+}
+}  // namespace
+
 int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, const double* f, double* x, const gmres_opts* opts, gmres_stats* st,
                 void* stream)
 {
     int code = DAFMM_OK;
     int r = guarded([&] {
-        if (!ops || !f || !x || !opts || !st) fail(DAFMM_EBADARG, "NULL argument");
-        if (opts->restart < 1 || opts->restart > 128) fail(DAFMM_EBADARG, "restart must lie in 1..128");
-        if (opts->max_iters < 0) fail(DAFMM_EBADARG, "max_iters must be >= 0");
-        if (!(opts->tol > 0)) fail(DAFMM_EBADARG, "tol must be positive");
-        if (opts->precision != DAFMM_FP64 && opts->precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
-        if (opts->precision == DAFMM_MIXED && !(opts->inner_tol > 0 && opts->inner_tol < 1))
-            fail(DAFMM_EBADARG, "inner_tol must lie in (0, 1) in mixed precision");
-        for (int v : opts->reserved)
-            if (v) fail(DAFMM_EBADARG, "reserved options must be zero");
-        if (f == x) fail(DAFMM_EBADARG, "f and x must not overlap");
+        check_gmres(ops, f, x, opts, st);
         PrecFn prec = nullptr;
         if (M) {
             if (hodlr_tree(M) != ops->tree) fail(DAFMM_EBADARG, "the preconditioner was built on another tree");
@@ -336,6 +372,15 @@ int dafmm_sync(dafmm_ops* ops, void* stream)
     return r;
 }
 
+int dafmm_set_contrast(dafmm_ops* ops, const double* q_dev, void* stream)
+{
+    return guarded([&] {
+        if (!ops || !q_dev) fail(DAFMM_EBADARG, "NULL argument");
+        cuda_check(cudaMemcpyAsync(ops->dev.q, q_dev, sizeof(double) * ops->tree->t.N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+                   "copy of q");
+    });
+}
+
 int dafmm_debug_stall(dafmm_ops* ops, int pass)
 {
     return guarded([&] {
@@ -393,6 +438,131 @@ int ops_destroy(dafmm_ops* ops)
     free_ops(ops->dev);
     delete ops;
     return DAFMM_OK;
+}
+
+int unet_create(const unet_params* p, dafmm_unet** out)
+{
+    return guarded([&] {
+        if (!p || !out) fail(DAFMM_EBADARG, "NULL argument");
+        *out = nullptr;
+        for (int v : p->reserved)
+            if (v) fail(DAFMM_EBADARG, "reserved parameters must be zero");
+        require_device();
+        *out = unet_new(*p);
+    });
+}
+
+int unet_destroy(dafmm_unet* net)
+{
+    return guarded([&] { unet_delete(net); });
+}
+
+int unet_num_params(const dafmm_unet* net, long* n)
+{
+    return guarded([&] {
+        if (!net || !n) fail(DAFMM_EBADARG, "NULL argument");
+        *n = unet_size(net);
+    });
+}
+
+int unet_get_params(const dafmm_unet* net, float* host)
+{
+    return guarded([&] {
+        if (!net || !host) fail(DAFMM_EBADARG, "NULL argument");
+        unet_get(net, host);
+    });
+}
+
+int unet_set_params(dafmm_unet* net, const float* host)
+{
+    return guarded([&] {
+        if (!net || !host) fail(DAFMM_EBADARG, "NULL argument");
+        unet_set(net, host);
+    });
+}
+
+int unet_forward(dafmm_unet* net, int batch, int height, int width, const float* in, float* out, void* stream)
+{
+    return guarded([&] {
+        if (!net || !in || !out) fail(DAFMM_EBADARG, "NULL argument");
+        unet_fwd(net, batch, height, width, in, out, (cudaStream_t)stream);
+    });
+}
+
+int unet_backward(dafmm_unet* net, int batch, int height, int width, const float* in, const float* target, float* out, double* loss,
+                  void* stream)
+{
+    return guarded([&] {
+        if (!net || !in || !target || !out || !loss) fail(DAFMM_EBADARG, "NULL argument");
+        *loss = unet_bwd(net, batch, height, width, in, target, out, (cudaStream_t)stream);
+    });
+}
+
+int unet_get_grads(const dafmm_unet* net, float* host)
+{
+    return guarded([&] {
+        if (!net || !host) fail(DAFMM_EBADARG, "NULL argument");
+        unet_get_grad(net, host);
+    });
+}
+
+int unet_adam(dafmm_unet* net, float lr, float beta1, float beta2, float eps, void* stream)
+{
+    return guarded([&] {
+        if (!net) fail(DAFMM_EBADARG, "NULL argument");
+        unet_adam_step(net, lr, beta1, beta2, eps, (cudaStream_t)stream);
+    });
+}
+
+int unet_guess(dafmm_unet* net, const dafmm_ops* ops, const double* f, double* x, void* stream)
+{
+    return guarded([&] {
+        if (!net || !ops || !f || !x) fail(DAFMM_EBADARG, "NULL argument");
+        if (f == x) fail(DAFMM_EBADARG, "f and x must not overlap");
+        unet_apply_nodes(net, ops->tree->t, ops->dev, f, x, 0.0, 1.0, (cudaStream_t)stream);
+    });
+}
+
+int gmres_solve_learned(dafmm_ops* ops, const dafmm_hodlr* M, dafmm_unet* net, int flags, double alpha, const double* f, double* x,
+                        const gmres_opts* opts, gmres_stats* st, learned_stats* ls, void* stream)
+{
+    int code = DAFMM_OK;
+    double* tmp = nullptr;
+    int r = guarded([&] {
+        check_gmres(ops, f, x, opts, st);
+        if (!net || !ls) fail(DAFMM_EBADARG, "NULL argument");
+        if (flags & ~3) fail(DAFMM_EBADARG, "unknown flags");
+        if (M && hodlr_tree(M) != ops->tree) fail(DAFMM_EBADARG, "the preconditioner was built on another tree");
+        const Tree& t = ops->tree->t;
+        cudaStream_t s = (cudaStream_t)stream;
+        ls->guess_used = 0;
+        ls->guess_residual = -1;
+        ls->corrections = 0;
+        if (flags & 1) {
+            // the network's guess, kept only if it beats x0 = 0
+            if (cudaMalloc(&tmp, sizeof(double2) * 2 * t.N) != cudaSuccess) {
+                cudaGetLastError();
+                fail(DAFMM_ENOMEM, "device allocation for the guess failed");
+            }
+            unet_apply_nodes(net, t, ops->dev, f, tmp, 0.0, 1.0, s);
+            ls->guess_residual = relative_residual(t, ops->dev, f, tmp, tmp + 2 * t.N, unet_scalars(net), s);
+            if (ls->guess_residual < 1.0) {
+                cuda_check(cudaMemcpyAsync(x, tmp, sizeof(double2) * t.N, cudaMemcpyDeviceToDevice, s), "cudaMemcpyAsync");
+                ls->guess_used = 1;
+            }
+        }
+        if (flags & 2) {
+            LearnedPrec lp{M, net, &t, &ops->dev, alpha, 0};
+            code = gmres_run(t, ops->dev, &lp, learned_prec, f, x, *opts, *st, s);
+            ls->corrections = lp.applies;
+        } else {
+            code = gmres_run(t, ops->dev, M, M ? hodlr_prec : nullptr, f, x, *opts, *st, s);
+        }
+        if (code == DAFMM_ENOTCONV)
+            fail(DAFMM_ENOTCONV, "GMRES reached max_iters at relative residual " + std::to_string(st->rel_residual));
+    });
+    cudaFree(tmp);
+    return r;
 }
 
 }  // extern "C"

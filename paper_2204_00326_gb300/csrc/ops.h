@@ -147,6 +147,23 @@ const dafmm_tree* hodlr_tree(const dafmm_hodlr* h);
 void hodlr_dense(const dafmm_hodlr* h, cd* out);
 void hodlr_shape(const dafmm_hodlr* h, long* N, int* levels, int* leaf, int* rank_max, double* seconds);
 
+// Learned guess (unet.cu)
+dafmm_unet* unet_new(const unet_params& p);
+void unet_delete(dafmm_unet* u);
+long unet_size(const dafmm_unet* u);
+void unet_get(const dafmm_unet* u, float* host);
+void unet_set(dafmm_unet* u, const float* host);
+void unet_get_grad(const dafmm_unet* u, float* host);
+void unet_fwd(dafmm_unet* u, int B, int H, int W, const float* in, float* out, cudaStream_t s);
+double unet_bwd(dafmm_unet* u, int B, int H, int W, const float* in, const float* target, float* out, cudaStream_t s);
+void unet_adam_step(dafmm_unet* u, float lr, float b1, float b2, float eps, cudaStream_t s);
+// x = a x + c s N(q, v / s) on the tree's node grid, s = max |v|
+void unet_apply_nodes(dafmm_unet* u, const Tree& t, const OpsDev& d, const double* v, double* x, double a, double c, cudaStream_t s);
+
+// |f - A x| / |f| with the FP64 operator; tmp: N complex128, scal: 2 device doubles
+double relative_residual(const Tree& t, OpsDev& d, const double* f, const double* x, double* tmp, double* scal, cudaStream_t s);
+double* unet_scalars(dafmm_unet* u);  // 2 device doubles owned by the network
+
 // Kernels one application launches.
 int launches_per_call(const Tree& t, const OpsDev& d, int precision);
 // Synchronise the stream and report (and clear) a device-side wait timeout.

@@ -119,6 +119,25 @@ class gmres_stats(ctypes.Structure):
     ]
 
 
+class unet_params(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int),
+        ("base", ctypes.c_int),
+        ("in_ch", ctypes.c_int),
+        ("out_ch", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+        ("reserved", ctypes.c_int * 8),
+    ]
+
+
+class learned_stats(ctypes.Structure):
+    _fields_ = [
+        ("guess_used", ctypes.c_int),
+        ("guess_residual", ctypes.c_double),
+        ("corrections", ctypes.c_int),
+    ]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_2204_00326_gb300.build()")
 lib = ctypes.CDLL(LIB_PATH)
@@ -136,6 +155,7 @@ _sig = {
     "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
+    "dafmm_set_contrast": ([_P, _P, _P], ctypes.c_int),
     "gmres_solve": ([_P, _P, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
     "hodlr_factor": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hodlr_solve": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -148,6 +168,18 @@ _sig = {
     "dafmm_profile": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_profile_read": ([_P, ctypes.POINTER(dafmm_profile_t)], ctypes.c_int),
     "ops_destroy": ([_P], ctypes.c_int),
+    "unet_create": ([ctypes.POINTER(unet_params), ctypes.POINTER(_P)], ctypes.c_int),
+    "unet_destroy": ([_P], ctypes.c_int),
+    "unet_num_params": ([_P, ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
+    "unet_get_params": ([_P, _P], ctypes.c_int),
+    "unet_set_params": ([_P, _P], ctypes.c_int),
+    "unet_forward": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "unet_backward": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "unet_get_grads": ([_P, _P], ctypes.c_int),
+    "unet_adam": ([_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P], ctypes.c_int),
+    "unet_guess": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "gmres_solve_learned": ([_P, _P, _P, ctypes.c_int, ctypes.c_double, _P, _P, ctypes.POINTER(gmres_opts),
+                             ctypes.POINTER(gmres_stats), ctypes.POINTER(learned_stats), _P], ctypes.c_int),
 }
 EXPORTS = tuple(_sig)
 for _name, (_args, _res) in _sig.items():
@@ -178,7 +210,7 @@ def _dptr(t, dtype_name: str) -> int:
         raise ValueError(f"expected a CUDA tensor of {dtype_name}")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
-    want = {"complex128": torch.complex128, "float64": torch.float64}[dtype_name]
+    want = {"complex128": torch.complex128, "float64": torch.float64, "float32": torch.float32}[dtype_name]
     if t.dtype != want:
         raise ValueError(f"expected dtype {want}, got {t.dtype}")
     return int(t.data_ptr())
@@ -249,6 +281,11 @@ def dafmm_matvec_noalloc(ops: int, v, out, precision: int = DAFMM_FP64, stream=N
 def dafmm_sync(ops: int, stream=None) -> None:
     """Synchronise and raise DafmmError(DAFMM_ETIMEOUT) if a device wait gave up."""
     _check(lib.dafmm_sync(ops, _stream_ptr(stream)))
+
+
+def dafmm_set_contrast(ops: int, q, stream=None) -> None:
+    """Replace the operator's contrast (N float64 on the device)."""
+    _check(lib.dafmm_set_contrast(ops, _dptr(q, "float64"), _stream_ptr(stream)))
 
 
 def dafmm_debug_stall(ops: int, pass_index: int) -> None:
@@ -336,3 +373,98 @@ def hodlr_destroy(M: int) -> None:
 
 def ops_destroy(ops: int) -> None:
     _check(lib.ops_destroy(ops))
+
+
+# --- learned guess ---------------------------------------------------------
+def unet_create(levels: int = 4, base: int = 32, seed: int = 0) -> int:
+    p = unet_params()
+    p.levels = levels
+    p.base = base
+    p.in_ch = 3
+    p.out_ch = 2
+    p.seed = seed
+    h = _P()
+    _check(lib.unet_create(ctypes.byref(p), ctypes.byref(h)))
+    return h.value
+
+
+def unet_destroy(net: int) -> None:
+    _check(lib.unet_destroy(net))
+
+
+def unet_num_params(net: int) -> int:
+    n = ctypes.c_long()
+    _check(lib.unet_num_params(net, ctypes.byref(n)))
+    return n.value
+
+
+def unet_get_params(net: int) -> np.ndarray:
+    a = np.zeros(unet_num_params(net), np.float32)
+    _check(lib.unet_get_params(net, a.ctypes.data))
+    return a
+
+
+def unet_set_params(net: int, params: np.ndarray) -> None:
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != unet_num_params(net):
+        raise ValueError("wrong number of parameters")
+    _check(lib.unet_set_params(net, a.ctypes.data))
+
+
+def unet_forward(net: int, x, out=None, stream=None):
+    """x: [batch, height, width, 3] float32 CUDA tensor; returns [batch, height, width, 2]."""
+    import torch
+
+    b, h, w, _ = x.shape
+    if out is None:
+        out = torch.empty((b, h, w, 2), dtype=torch.float32, device=x.device)
+    _check(lib.unet_forward(net, b, h, w, _dptr(x, "float32"), _dptr(out, "float32"), _stream_ptr(stream)))
+    return out
+
+
+def unet_backward(net: int, x, target, out=None, stream=None):
+    """Forward, mean squared error against target, parameter gradients. Returns (loss, out)."""
+    import torch
+
+    b, h, w, _ = x.shape
+    if out is None:
+        out = torch.empty((b, h, w, 2), dtype=torch.float32, device=x.device)
+    loss = ctypes.c_double()
+    _check(lib.unet_backward(net, b, h, w, _dptr(x, "float32"), _dptr(target, "float32"), _dptr(out, "float32"),
+                             ctypes.byref(loss), _stream_ptr(stream)))
+    return loss.value, out
+
+
+def unet_get_grads(net: int) -> np.ndarray:
+    a = np.zeros(unet_num_params(net), np.float32)
+    _check(lib.unet_get_grads(net, a.ctypes.data))
+    return a
+
+
+def unet_adam(net: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    _check(lib.unet_adam(net, lr, beta1, beta2, eps, _stream_ptr(stream)))
+
+
+def unet_guess(net: int, ops: int, f, x, stream=None) -> None:
+    _check(lib.unet_guess(net, ops, _dptr(f, "complex128"), _dptr(x, "complex128"), _stream_ptr(stream)))
+
+
+def gmres_solve_learned(ops: int, net: int, f, x, flags: int = 1, alpha: float = 1.0, tol: float = 1e-8,
+                        precision: int = DAFMM_FP64, restart: int = 50, max_iters: int = 1000, inner_tol: float = 1e-5,
+                        M: int | None = None, stream=None):
+    """gmres_solve with the network's initial guess (flags bit 0) and/or coarse
+    correction (bit 1).  Returns (status, gmres_stats, learned_stats)."""
+    o = gmres_opts()
+    o.restart = restart
+    o.max_iters = max_iters
+    o.tol = tol
+    o.precision = precision
+    o.inner_tol = inner_tol
+    st = gmres_stats()
+    ls = learned_stats()
+    rc = lib.gmres_solve_learned(ops, M, net, flags, alpha, _dptr(f, "complex128"), _dptr(x, "complex128"), ctypes.byref(o),
+                                 ctypes.byref(st), ctypes.byref(ls), _stream_ptr(stream))
+    if rc not in (DAFMM_OK, DAFMM_ENOTCONV):
+        _check(rc)
+    return rc, st, ls
+

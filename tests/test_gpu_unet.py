@@ -1,0 +1,201 @@
+"""The learned-guess network on the GPU against the FP64 reference, and its use.
+
+Tolerances: the kernels round weights, inputs and activations to BF16 (unit
+roundoff u = 2^-8) before every product and sum in FP32.  The reference takes
+the same rounding of weights and inputs (exact in FP64); rounding errors of
+the activations of the ~D layers a value passes through then add up like a
+random walk, so the relative error of the output is about sqrt(D) u and that
+of a gradient (forward, then backward through as many layers) about
+sqrt(3 D) u; with D = 18 convolutions that is 1.7e-2 and 2.9e-2.  The tests
+allow 5e-2 on the whole output and the whole gradient, 2e-1 per layer.
+Gradients are compared on the loss |N(x)|^2 / n (zero target): with random
+targets the gradient entries are sums of many terms of both signs whose
+cancellation amplifies the same rounding errors several times on small
+networks; the loss value itself is checked with random targets.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import unet as U  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 5e-2
+
+
+@pytest.fixture(scope="module")
+def N():
+    import paper_2204_00326_gb300 as pkg
+
+    pkg.build()
+    from paper_2204_00326_gb300 import native
+
+    return native
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _bf16(a):
+    """Round float32 values to the nearest BF16 (ties to even), as float32."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("levels,base", [(2, 4), (4, 8)])
+def test_forward_and_gradient_match_fp64_reference(N, levels, base):
+    net = N.unet_create(levels=levels, base=base, seed=3)
+    try:
+        assert N.unet_num_params(net) == U.num_params(levels, base)
+        theta = U.init(levels, base, seed=7).astype(np.float32)
+        N.unet_set_params(net, theta)
+        assert np.array_equal(N.unet_get_params(net), theta)
+        rng = np.random.default_rng(5)
+        H, W = 8 << (levels - 1), 4 << levels
+        x = rng.standard_normal((2, H, W, 3)).astype(np.float32)
+        t = rng.standard_normal((2, H, W, 2)).astype(np.float32)
+        th64 = _bf16(theta).astype(np.float64)
+        x64 = _bf16(x).astype(np.float64)
+        y_ref = U.forward(th64, x64, levels, base)
+        y = N.unet_forward(net, torch.as_tensor(x, device="cuda")).cpu().numpy()
+        assert _rel(y, y_ref) < TOL
+        loss_ref, _ = U.loss_and_grad(th64, x64, t.astype(np.float64), levels, base)
+        loss, y2 = N.unet_backward(net, torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"))
+        assert abs(loss - loss_ref) < TOL * loss_ref
+        assert np.allclose(y2.cpu().numpy(), y, rtol=0, atol=0)
+        zero = np.zeros_like(t)
+        loss_ref, g_ref = U.loss_and_grad(th64, x64, zero.astype(np.float64), levels, base)
+        loss, _ = N.unet_backward(net, torch.as_tensor(x, device="cuda"), torch.as_tensor(zero, device="cuda"))
+        assert abs(loss - loss_ref) < TOL * loss_ref
+        g = N.unet_get_grads(net)
+        assert _rel(g, g_ref) < TOL
+        # every convolution's block of the gradient, not only the largest ones
+        off = 0
+        for ci, co, K in U.conv_specs(levels, base):
+            n = K * K * ci * co + co
+            assert _rel(g[off:off + n], g_ref[off:off + n]) < 4 * TOL, (ci, co, K)
+            off += n
+    finally:
+        N.unet_destroy(net)
+
+
+def test_adam_step_follows_its_formula(N):
+    net = N.unet_create(levels=2, base=4, seed=1)
+    try:
+        rng = np.random.default_rng(2)
+        x = torch.as_tensor(rng.standard_normal((1, 8, 8, 3)).astype(np.float32), device="cuda")
+        t = torch.as_tensor(rng.standard_normal((1, 8, 8, 2)).astype(np.float32), device="cuda")
+        p0 = N.unet_get_params(net).astype(np.float64)
+        N.unet_backward(net, x, t)
+        g = N.unet_get_grads(net).astype(np.float64)
+        lr, b1, b2, eps = 1e-2, 0.9, 0.999, 1e-8
+        N.unet_adam(net, lr, b1, b2, eps)
+        torch.cuda.synchronize()
+        p1 = N.unet_get_params(net).astype(np.float64)
+        # first step from zero moments: m^ = g, v^ = g^2
+        ref = p0 - lr * g / (np.abs(g) + eps)
+        assert np.allclose(p1, ref, rtol=1e-5, atol=1e-6 * lr)
+    finally:
+        N.unet_destroy(net)
+
+
+def test_argument_errors(N):
+    with pytest.raises(N.DafmmError):
+        N.unet_create(levels=0)
+    net = N.unet_create(levels=3, base=4)
+    try:
+        with pytest.raises(N.DafmmError):  # sides must be multiples of 2^(levels-1)
+            N.unet_forward(net, torch.zeros((1, 6, 8, 3), device="cuda"))
+        with pytest.raises(ValueError):
+            N.unet_set_params(net, np.zeros(3, np.float32))
+    finally:
+        N.unet_destroy(net)
+
+
+def test_training_fits_a_fixed_batch(N):
+    net = N.unet_create(levels=3, base=8, seed=2)
+    try:
+        rng = np.random.default_rng(3)
+        x = torch.as_tensor(rng.standard_normal((4, 16, 16, 3)).astype(np.float32), device="cuda")
+        # a smooth target the network can represent: local averages of the input
+        xt = x.cpu().numpy()
+        tgt = np.stack([xt[..., 0] * xt[..., 1], xt[..., 2] - xt[..., 0]], axis=-1).astype(np.float32)
+        t = torch.as_tensor(tgt, device="cuda")
+        first = None
+        for k in range(300):
+            loss, _ = N.unet_backward(net, x, t)
+            first = loss if first is None else first
+            N.unet_adam(net, 3e-3)
+        assert loss < 0.1 * first, (first, loss)
+    finally:
+        N.unet_destroy(net)
+
+
+def test_learned_guess_is_accepted_and_costs_no_iterations(N):
+    """Trained on 256 solver solutions (64 x 64, kappa = 20), the guess of a
+    held-out problem is accepted with |f - A x0| / |f| < 0.5 (a zero guess
+    has 1); HODLR-preconditioned GMRES from it needs no more iterations than
+    from zero; the nonlinear coarse correction inside flexible GMRES
+    converges.  (How many iterations the guess saves is measured, not
+    asserted: bench.py --learned.)"""
+    from paper_2204_00326_gb300 import learned as Lr
+    from paper_2204_00326_gb300.operator import DafmmOperator
+
+    n, kappa = 64, 20.0
+    X, Y, _ = Lr.generate(n, kappa, count=256, seed=100)
+    net = N.unet_create(levels=4, base=16, seed=4)
+    try:
+        losses, _ = Lr.train(net, X, Y, steps=1500, batch=8, lr=2e-3, lr_final=2e-4)
+        assert np.mean(losses[-50:]) < 0.25 * np.mean(losses[:20])
+        op = DafmmOperator(n, kappa, np.zeros(n * n))
+        try:
+            q, f = Lr.problem(op.xy, kappa, 8, seed=9999)
+            N.dafmm_set_contrast(op.ops, torch.as_tensor(q, device="cuda"))
+            M = N.hodlr_factor(op.ops, rank=15, leaf_size=64)
+            try:
+                res = Lr.compare(op, net, f, M, tol=1e-8)
+                z, g = res["zero_guess"], res["learned_guess"]
+                assert z["converged"] and g["converged"] and g["rel_residual"] <= 1e-8
+                assert g["guess_used"] and 0 < g["guess_residual"] < 0.5, res
+                assert g["iterations"] <= z["iterations"], res
+                fd = torch.as_tensor(f, device="cuda")
+                x = torch.zeros_like(fd)
+                rc, st, ls = N.gmres_solve_learned(op.ops, net, fd, x, flags=3, alpha=0.25, tol=1e-8, M=M, max_iters=500)
+                assert rc == N.DAFMM_OK and st.rel_residual <= 1e-8 and ls.corrections == st.precond_applies > 0
+            finally:
+                N.hodlr_destroy(M)
+        finally:
+            op.close()
+    finally:
+        N.unet_destroy(net)
+
+
+def test_guess_rejected_when_worse_than_zero(N):
+    """An untrained network's guess is worse than x0 = 0 and is not used."""
+    from paper_2204_00326_gb300 import learned as Lr
+    from paper_2204_00326_gb300.operator import DafmmOperator
+
+    n, kappa = 32, 8.0
+    net = N.unet_create(levels=3, base=4, seed=11)
+    op = DafmmOperator(n, kappa, np.zeros(n * n))
+    try:
+        q, f = Lr.problem(op.xy, kappa, 4, seed=5)
+        N.dafmm_set_contrast(op.ops, torch.as_tensor(q, device="cuda"))
+        # scale the output layer so that the guess is far off
+        p = N.unet_get_params(net)
+        p[-(2 + 2 * 4):] *= 50.0
+        N.unet_set_params(net, p)
+        fd = torch.as_tensor(f, device="cuda")
+        x = torch.zeros_like(fd)
+        rc, st, ls = N.gmres_solve_learned(op.ops, net, fd, x, flags=1, tol=1e-10, max_iters=400)
+        assert rc == N.DAFMM_OK and ls.guess_residual > 1 and ls.guess_used == 0
+        x0 = torch.zeros_like(fd)
+        rc0, st0, _ = N.gmres_solve(op.ops, fd, x0, tol=1e-10, max_iters=400)
+        assert st.iterations == st0.iterations
+    finally:
+        op.close()
+        N.unet_destroy(net)

@@ -365,7 +365,7 @@ def main():
     # dominant kernel: the fused far field (every tree pass in one cooperative launch)
     calls = max(1, prof_mixed.calls)
     ms_far = prof_mixed.ms_far / calls
-    cmacs_far = st.cmacs_up + st.cmacs_m2l + st.cmacs_down
+    cmacs_far = st.cmacs_far_fused  # realised entries the kernel streams (its operators, see dafmm_stats_t)
     # operators read once (complex64), coefficients written and read once (complex64), the input read (complex128)
     bytes_far = cmacs_far * 8.0 + st.coef_bytes_per_rhs / 2.0 + 16.0 * w.N
     achieved = bytes_far / (ms_far * 1e-3) / 1e9

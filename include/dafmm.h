@@ -102,6 +102,10 @@ typedef struct dafmm_stats_t {
                                      read once each, complex128 */
     int launches_per_call;        /* kernels one dafmm_matvec launches (mixed) */
     int launches_per_call_fp64;   /* ... in FP64 */
+    double cmacs_far_fused;       /* per application with one RHS: complex multiply-adds of the
+                                     far-field kernel (its level L-1 up pass reads the leaf values
+                                     through the P2M; the last L2L is left to the leaf kernel) */
+    double cmacs_leaf_fused;      /* ... of the leaf kernel: near field, L2P, L2L composed with L2P */
 } dafmm_stats_t;
 
 /*

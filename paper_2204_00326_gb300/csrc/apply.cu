@@ -1085,8 +1085,11 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
 // Morton order (a 2 x 2 quad); the inputs of the 4 x 4 leaves around it are
 // read in complex128, rounded to T once and kept in shared memory (FP64
 // conversions are scarce on this GPU).  The leaves' locals are lc (+ lc2 when
-// not null).  done (not null): row and piece counters of the fused launch
-// before, reset here for the next application.
+// not null).  c_* (not null): blocks of the L2L from the parent level composed
+// with L2P (16 x ri, column stride 16) applied by the second thread group to
+// the parent level's locals lcA (+ lcB when not null), stride ldc.  done (not
+// null): row and piece counters of the fused launch before, reset here for
+// the next application.
 constexpr int kLeafPerCta = 4;
 
 template <typename T>
@@ -1097,6 +1100,11 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
                                                                       const typename V2<T>::t* __restrict__ l2p, int ldl,
                                                                       const typename V2<T>::t* __restrict__ lc,
                                                                       const typename V2<T>::t* __restrict__ lc2,
+                                                                      const int* __restrict__ c_rowptr, const int* __restrict__ c_col,
+                                                                      const long* __restrict__ c_moff, const int* __restrict__ c_rin,
+                                                                      const typename V2<T>::t* __restrict__ cm, int ldc,
+                                                                      const typename V2<T>::t* __restrict__ lcA,
+                                                                      const typename V2<T>::t* __restrict__ lcB,
                                                                       const double2* __restrict__ v, const double* __restrict__ q, double k2,
                                                                       double2* __restrict__ out, int* __restrict__ done)
 {
@@ -1161,6 +1169,34 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
             for (int j = 0; j < 16; j += 2) {
                 cmac<T>(ar0, ai0, B[j * 16], vs[j]);
                 cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
+            }
+        }
+        if (grp == 1 && c_rowptr != nullptr) {
+            // L2L from the parent level composed with L2P: 16 x ri blocks on the parent's locals (lcA + lcB)
+            for (int e = c_rowptr[leaf]; e < c_rowptr[leaf + 1]; e++) {
+                const C* U = cm + c_moff[e] + i;
+                const C* u = lcA + (size_t)c_col[e] * ldc;
+                const C* u2 = lcB ? lcB + (size_t)c_col[e] * ldc : nullptr;
+                const int ri = c_rin[e];
+                for (int j0 = 0; j0 < ri; j0 += 16) {
+                    C uj[16], Uj[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++)
+                        if (j0 + j < ri) {
+                            uj[j] = u[j0 + j];
+                            Uj[j] = U[(j0 + j) * 16];
+                            if (u2) {
+                                const C w = u2[j0 + j];
+                                uj[j].x += w.x;
+                                uj[j].y += w.y;
+                            }
+                        }
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        if (j0 + j < ri) cmac<T>(ar0, ai0, Uj[j], uj[j]);
+                        if (j0 + j + 1 < ri) cmac<T>(ar1, ai1, Uj[j + 1], uj[j + 1]);
+                    }
+                }
             }
         }
         if (grp == 2 && l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {
@@ -1391,6 +1427,80 @@ int fused_ctas()
     return std::max(1, sms * std::max(per_sm, 1));
 }
 
+// C = A B for column-major blocks: A is m x k (column stride lda), B is k x n
+// (column stride ldb), C is m x n (column stride ldc).
+void block_mul(const cd* A, int lda, const cd* B, int ldb, cd* C, int ldc, int m, int k, int n)
+{
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < m; i++) {
+            cd s = 0;
+            for (int l = 0; l < k; l++) s += A[(size_t)l * lda + i] * B[(size_t)j * ldb + l];
+            C[(size_t)j * ldc + i] = s;
+        }
+}
+
+// The up pass of level L-1 composed with the leaves' P2M: every block
+// T_e (ro x ro_c, child leaf c) becomes T_e V_c (ro x 16), V_c the P2M block
+// of leaf c, so the multipoles of level L-1 come straight from the leaf values.
+BsrHost compose_up(const BsrHost& T, const BsrHost& V)
+{
+    BsrHost C;
+    C.nrows = T.nrows;
+    C.Rout = T.Rout;
+    C.Rin = 16;
+    C.rowptr = T.rowptr;
+    C.rout = T.rout;
+    C.col.resize(T.col.size());
+    C.rin.assign(T.col.size(), 16);
+    for (size_t e = 0; e < T.col.size(); e++) {
+        const int c = T.col[e];
+        C.col[e] = c;  // leaf slot = leaf
+        if (T.rin[e] == 0) continue;
+        if (V.rowptr[c + 1] - V.rowptr[c] != 1 || V.rin[V.rowptr[c]] != 16 || V.rout[c] != T.rin[e] || V.col[V.rowptr[c]] != c)
+            fail(DAFMM_EBADARG, "composing P2M: a leaf row is not one 16-column block of the child's rank");
+    }
+    C.layout();
+    for (int r = 0; r < T.nrows; r++)
+        for (int e = T.rowptr[r]; e < T.rowptr[r + 1]; e++) {
+            const int c = T.col[e];
+            if (T.rin[e] == 0 || T.rout[r] == 0) continue;  // zero block (layout zeroes mats)
+            const int ev = V.rowptr[c];
+            block_mul(&T.mats[T.moff[e]], T.ld[r], &V.mats[V.moff[ev]], V.ld[c], &C.mats[C.moff[e]], C.ld[r], T.rout[r], T.rin[e], 16);
+        }
+    return C;
+}
+
+// The L2L into the leaves composed with their L2P: every block D_e (ri_b x
+// ri_s, parent slot s) of leaf b becomes U_b D_e (16 x ri_s), U_b the L2P
+// block of leaf b, so the leaf values come straight from the parent's locals.
+BsrHost compose_leaf(const BsrHost& D, const BsrHost& U)
+{
+    BsrHost C;
+    C.nrows = D.nrows;
+    C.Rout = 16;
+    C.Rin = D.Rin;
+    C.rowptr = D.rowptr;
+    C.col = D.col;
+    C.rin = D.rin;
+    C.rout.assign(D.nrows, 0);
+    for (int b = 0; b < D.nrows; b++) {
+        if (D.rowptr[b + 1] == D.rowptr[b]) continue;
+        C.rout[b] = 16;
+        if (D.rout[b] == 0) continue;
+        if (U.rowptr[b + 1] - U.rowptr[b] != 1 || U.rout[b] != 16 || U.rin[U.rowptr[b]] != D.rout[b])
+            fail(DAFMM_EBADARG, "composing L2P: a leaf row is not one 16-row block of the leaf's rank");
+    }
+    C.layout();
+    for (int b = 0; b < D.nrows; b++) {
+        if (D.rout[b] == 0) continue;  // zero blocks (layout zeroes mats)
+        for (int e = D.rowptr[b]; e < D.rowptr[b + 1]; e++) {
+            const int eu = U.rowptr[b];
+            block_mul(&U.mats[U.moff[eu]], U.ld[b], &D.mats[D.moff[e]], D.ld[b], &C.mats[C.moff[e]], C.ld[b], 16, D.rout[b], D.rin[e]);
+        }
+    }
+    return C;
+}
+
 // Warp shares of a plan's chain list for a grid of `warps` warps: chunks per
 // warp in each phase, and the shares in the phases before.  Returns the shares.
 int fused_shares(const FusedPlan& F, int warps, int* kpw, int* sbase)
@@ -1415,7 +1525,7 @@ int fused_shares(const FusedPlan& F, int warps, int* kpw, int* sbase)
 // read is on the chain.  Every row a chunk reads lies in an earlier phase (or
 // in a bulk pass whose inputs do), and a warp works through its shares phase
 // by phase, so the waits cannot form a cycle.
-void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
+void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
 {
     Fused& F = d.fz;
     const int L = t.L, top = t.top;
@@ -1426,6 +1536,14 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
     std::vector<int> up_i(L + 1, -1), m2l_i(L + 1, -1), down_i(L + 1, -1);
     for (int nu = L; nu >= top; nu--) {
         up_i[nu] = (int)passes.size();
+        if (nu == L - 1 && upc) {
+            // multipoles of level L-1 straight from the leaf values
+            passes.push_back(PassRef{nu, 3});
+            hs.push_back(upc);
+            ldx.push_back(16);
+            deps.push_back(0u);
+            continue;
+        }
         passes.push_back(PassRef{nu, 0});
         hs.push_back(&h.lv[nu].up);
         ldx.push_back(nu == L ? 16 : h.lv[nu + 1].Ro);
@@ -1438,7 +1556,8 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
         ldx.push_back(h.lv[nu].Ro);
         deps.push_back(1u << up_i[nu]);
     }
-    for (int nu = top; nu < L; nu++) {
+    // the L2L from level L-1 is composed with L2P in the leaf kernel
+    for (int nu = top; nu < L - 1; nu++) {
         down_i[nu] = (int)passes.size();
         passes.push_back(PassRef{nu, 2});
         hs.push_back(&h.lv[nu].down);
@@ -1553,8 +1672,12 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d)
     }
     F.deps = deps;
     F.target.assign(np, 0);
+    F.cmacs = 0;
     for (int p = 0; p < np; p++)
-        for (int r = 0; r < hs[p]->nrows; r++) F.target[p] += chunks(p, r) > 0;
+        for (int r = 0; r < hs[p]->nrows; r++) {
+            F.target[p] += chunks(p, r) > 0;
+            F.cmacs += (double)hs[p]->rout[r] * (cuts[p].cbase[r + 1] - cuts[p].cbase[r]);
+        }
     F.g.passes = passes;
     F.g.accumulate = 0;
     for (int p = 0; p < np; p++) upload_tables(F.g, cuts[p]);
@@ -1645,7 +1768,7 @@ PassArgs<T> fused_pass_args(const Tree& t, const OpsDev& d, const FBufs<T>& b, c
     const PassRef& pr = g.passes[p];
     const int nu = pr.level;
     const LevelDev& l = d.lv[nu];
-    const BsrDev& bs = pr.kind == 0 ? l.up : (pr.kind == 1 ? l.m2l : l.down);
+    const BsrDev& bs = pr.kind == 0 ? l.up : (pr.kind == 1 ? l.m2l : (pr.kind == 2 ? l.down : l.upc));
     PassArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.rout = bs.rout;
@@ -1653,8 +1776,8 @@ PassArgs<T> fused_pass_args(const Tree& t, const OpsDev& d, const FBufs<T>& b, c
     a.cbase = g.cbase[p];
     a.xmap = g.xmap[p];
     a.mats = (const C*)(sizeof(T) == 8 ? bs.m64 : bs.m32);
-    if (pr.kind == 0) {
-        if (nu == t.L)
+    if (pr.kind == 0 || pr.kind == 3) {
+        if (nu == t.L || pr.kind == 3)
             a.xd = (const double2*)v;
         else
             a.x = b.mp[nu + 1];
@@ -1765,11 +1888,14 @@ void run_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const double* 
     mark(prof, 3, s);
     const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
     const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
+    const bool comp = far && L - 1 >= t.top;
+    const C* cm = comp ? (const C*)(sizeof(T) == 8 ? d.leafc.m64 : d.leafc.m32) : nullptr;
     leaf_apply_kernel<T><<<(unsigned)((nleaf + kLeafPerCta - 1) / kLeafPerCta), 48 * kLeafPerCta, 0, s>>>(
         nleaf, d.nbr, nearp, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
-        l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
-        far && L > t.top ? b.lcd[L] : nullptr, (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out,
-        far ? d.fz.done : nullptr);
+        l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr, nullptr,
+        comp ? d.leafc.rowptr : nullptr, comp ? d.leafc.col : nullptr, comp ? d.leafc.moff : nullptr, comp ? d.leafc.rin : nullptr, cm,
+        comp ? d.lv[L - 1].Ri : 0, comp ? b.lc[L - 1] : nullptr, comp && L - 1 > t.top ? b.lcd[L - 1] : nullptr, (const double2*)v, d.q,
+        t.prm.kappa * t.prm.kappa, (double2*)out, far ? d.fz.done : nullptr);
     CK(cudaGetLastError());
     mark(prof, 4, s);
 }
@@ -1898,7 +2024,23 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
         CK(cudaFuncSetAttribute(stream_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, StreamCfg<double>::kCta));
         d.fz.ctas[0] = fused_ctas<double>();
         d.fz.ctas[1] = fused_ctas<float>();
-        build_fused(t, h, d);
+        // single right-hand side: the first up pass above the leaves reads the leaf
+        // values through the P2M, the last L2L is applied with L2P by the leaf kernel
+        BsrHost upc, leafc;
+        const bool compose = t.top <= L - 1;
+        if (compose) {
+            upc = compose_up(h.lv[L - 1].up, h.lv[L].up);
+            leafc = compose_leaf(h.lv[L - 1].down, h.lv[L].down);
+        }
+        build_fused(t, h, d, compose ? &upc : nullptr);
+        d.fz.leaf_cmacs = 144.0 * t.N;
+        for (int b = 0; b < h.lv[L].down.nrows; b++)
+            for (int e = h.lv[L].down.rowptr[b]; e < h.lv[L].down.rowptr[b + 1]; e++) d.fz.leaf_cmacs += 16.0 * h.lv[L].down.rin[e];
+        if (compose) {
+            for (size_t e = 0; e < leafc.rin.size(); e++) d.fz.leaf_cmacs += 16.0 * leafc.rin[e];
+            upload_bsr(upc, d.lv[L - 1].upc);
+            upload_bsr(leafc, d.leafc);
+        }
         for (int nu = t.top; nu <= L; nu++) {
             // single-right-hand-side coefficients, zero once: rows no pass writes read as zero
             LevelDev& l = d.lv[nu];
@@ -2024,10 +2166,12 @@ void free_ops(OpsDev& d)
     for (cudaEvent_t e : d.placeholder)
         if (e) cudaEventDestroy(e);
     if (d.cap_stream) cudaStreamDestroy(d.cap_stream);
+    free_bsr(d.leafc);
     for (auto& l : d.lv) {
         free_bsr(l.up);
         free_bsr(l.m2l);
         free_bsr(l.down);
+        free_bsr(l.upc);
         cudaFree(l.mp64);
         cudaFree(l.lc64);
         cudaFree(l.mp32);

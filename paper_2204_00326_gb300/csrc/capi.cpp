@@ -217,6 +217,8 @@ int build_nca_operators(dafmm_tree* tree, const double* q_dev, void* stream, daf
         upload_ops(t, h, ops->dev);
         ops->stats.launches_per_call = launches_per_call(t, ops->dev, DAFMM_MIXED);
         ops->stats.launches_per_call_fp64 = launches_per_call(t, ops->dev, DAFMM_FP64);
+        ops->stats.cmacs_far_fused = ops->dev.fz.cmacs;
+        ops->stats.cmacs_leaf_fused = ops->dev.fz.leaf_cmacs;
         double* q = nullptr;
         if (cudaMalloc(&q, sizeof(double) * t.N) != cudaSuccess) {
             cudaGetLastError();

@@ -15,6 +15,7 @@ namespace dafmm {
 struct LevelDev {
     int Ri = 0, Ro = 0;  // strides of the local / multipole buffers
     BsrDev up, m2l, down;
+    BsrDev upc;  // level L-1 only: its up pass composed with the leaves' P2M (reads the input vector)
     // coefficient scratch, grown with nrhs: multipoles [slot][Ro][nrhs], locals [slot][Ri][nrhs]
     void* mp64 = nullptr;
     void* lc64 = nullptr;
@@ -33,7 +34,7 @@ struct LevelDev {
 // partials in a fixed order.
 struct PassRef {
     int level = 0;
-    int kind = 0;  // 0 up (P2M/M2M), 1 M2L, 2 down (L2L)
+    int kind = 0;  // 0 up (P2M/M2M), 1 M2L, 2 down (L2L), 3 up of level L-1 composed with P2M
 };
 
 struct Group {
@@ -78,6 +79,8 @@ struct Fused {
     FusedPlan plan[2];             // [0] complex128, [1] complex64
     int ctas[2] = {0, 0};          // persistent grid, [0] complex128, [1] complex64
     int* done = nullptr;           // per pass: rows written in the running application; then the piece counter
+    double cmacs = 0;              // complex multiply-adds of one launch (realised ranks)
+    double leaf_cmacs = 0;         // ... of the leaf kernel after it (near field, L2P, composed L2L)
 };
 
 // One captured application (per precision), replayed while the vector
@@ -99,6 +102,7 @@ struct OpsDev {
     Group m2l;                  // every level at once
     std::vector<Group> down;    // per level (index = parent level)
     Fused fz;                   // single right-hand side: every pass in one launch
+    BsrDev leafc;               // rows leaves: the L2L from level L-1 composed with L2P (16 x R per block)
     double2* near64 = nullptr;  // 9 x 16 x 16, source offset (sx,sy) -> (sy+1)*3+(sx+1)
     float2* near32 = nullptr;
     int* nbr = nullptr;         // [nleaf][9] source leaf of each near offset, -1 outside

@@ -79,6 +79,8 @@ class dafmm_stats_t(ctypes.Structure):
         ("coef_bytes_per_rhs", ctypes.c_double),
         ("launches_per_call", ctypes.c_int),
         ("launches_per_call_fp64", ctypes.c_int),
+        ("cmacs_far_fused", ctypes.c_double),
+        ("cmacs_leaf_fused", ctypes.c_double),
     ]
 
 

@@ -1079,7 +1079,9 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
 
 // out = v + kappa^2 q (U_B u^{B,i} + sum_{9 offsets} T_o v_{B+o}) per leaf.
 // 48 threads per leaf: node i and one row sy of the 3 x 3 near offsets each;
-// the third group also does L2P; the groups' sums meet in shared memory.
+// before the near field the first group stages shared memory while the
+// second applies the composed L2L and L2P and the third L2P; the groups' sums
+// meet in shared memory.
 // 4 leaves per CTA.  Near blocks are stored [o][j][i] (target index fastest)
 // for conflict-free shared reads.  A CTA's four leaves are consecutive in
 // Morton order (a 2 x 2 quad); the inputs of the 4 x 4 leaves around it are
@@ -1121,63 +1123,65 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
         return c;
     };
     const int q0 = blockIdx.x * kLeafPerCta;
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
-        // block position (bx, by) seen from quad leaf l = (bx >= 2) + 2 (by >= 2) at offset (sx, sy)
-        const int pos = t >> 4, j = t & 15;
-        const int bx = pos & 3, by = pos >> 2;
-        const int l = (bx >= 2 ? 1 : 0) | (by >= 2 ? 2 : 0);
-        const int sx = bx - 1 - (l & 1), sy = by - 1 - (l >> 1);
-        const int src = q0 + l < nleaf ? nbr[(q0 + l) * 9 + (sy + 1) * 3 + (sx + 1)] : -1;
-        C val;
-        val.x = 0;
-        val.y = 0;
-        if (src >= 0) val = rnd(v[(size_t)src * 16 + j]);
-        vq[pos][j] = val;
-    }
-    {
-        // 16-byte loads, all issued before any is used
-        constexpr int kVec = 9 * 256 * (int)sizeof(C) / 16;
-        constexpr int kPer = (kVec + 48 * kLeafPerCta - 1) / (48 * kLeafPerCta);
-        const uint4* src = (const uint4*)near;
-        uint4* dst = (uint4*)sn;
-        uint4 tmp[kPer];
-#pragma unroll
-        for (int u = 0; u < kPer; u++) {
-            const int k = threadIdx.x + u * 48 * kLeafPerCta;
-            if (k < kVec) tmp[u] = src[k];
-        }
-#pragma unroll
-        for (int u = 0; u < kPer; u++) {
-            const int k = threadIdx.x + u * 48 * kLeafPerCta;
-            if (k < kVec) dst[k] = tmp[u];
-        }
-    }
-    __syncthreads();
-    const int grp = threadIdx.x / (16 * kLeafPerCta);  // offset row sy = grp - 1
+    const int grp = threadIdx.x / (16 * kLeafPerCta);  // offset row sy = grp - 1 of the near field
     const int li = threadIdx.x % (16 * kLeafPerCta);
     const int leaf = blockIdx.x * kLeafPerCta + li / 16;
     const int i = li & 15;
     T ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
-    if (leaf < nleaf) {
-        const int l = leaf - q0;
+    // The first group stages the near-field blocks and inputs in shared memory
+    // (and loads the epilogue's v, q) while the other two apply the far field,
+    // which needs no shared memory: the composed L2L and L2P (second), L2P (third).
+    double2 vv = make_double2(0, 0);
+    double qq = 0;
+    if (grp == 0) {
+        const int t0 = li;  // 0 .. 16 kLeafPerCta - 1
+        constexpr int kThr = 16 * kLeafPerCta;
+        if (leaf < nleaf) {
+            vv = v[(size_t)leaf * 16 + i];
+            qq = q[(size_t)leaf * 16 + i];
+        }
+        for (int t = t0; t < 256; t += kThr) {
+            // block position (bx, by) seen from quad leaf l = (bx >= 2) + 2 (by >= 2) at offset (sx, sy)
+            const int pos = t >> 4, j = t & 15;
+            const int bx = pos & 3, by = pos >> 2;
+            const int l = (bx >= 2 ? 1 : 0) | (by >= 2 ? 2 : 0);
+            const int sx = bx - 1 - (l & 1), sy = by - 1 - (l >> 1);
+            const int src = q0 + l < nleaf ? nbr[(q0 + l) * 9 + (sy + 1) * 3 + (sx + 1)] : -1;
+            C val;
+            val.x = 0;
+            val.y = 0;
+            if (src >= 0) val = rnd(v[(size_t)src * 16 + j]);
+            vq[pos][j] = val;
+        }
+        // 16-byte loads, several in flight per thread
+        constexpr int kVec = 9 * 256 * (int)sizeof(C) / 16;
+        constexpr int kIn = sizeof(C) == 16 ? 4 : 8;
+        const uint4* src = (const uint4*)near;
+        uint4* dst = (uint4*)sn;
+        for (int k0 = 0; k0 < kVec; k0 += kIn * kThr) {
+            uint4 tmp[kIn];
 #pragma unroll
-        for (int sx = 0; sx < 3; sx++) {
-            const int o = grp * 3 + sx;  // offset (sx - 1, grp - 1); outside the domain vq holds zeros
-            const C* vs = vq[(1 + (l >> 1) + grp - 1) * 4 + 1 + (l & 1) + sx - 1];
-            const C* B = sn + o * 256 + i;
+            for (int u = 0; u < kIn; u++) {
+                const int k = k0 + t0 + u * kThr;
+                if (k < kVec) tmp[u] = src[k];
+            }
 #pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-                cmac<T>(ar0, ai0, B[j * 16], vs[j]);
-                cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
+            for (int u = 0; u < kIn; u++) {
+                const int k = k0 + t0 + u * kThr;
+                if (k < kVec) dst[k] = tmp[u];
             }
         }
-        if (grp == 1 && c_rowptr != nullptr) {
-            // L2L from the parent level composed with L2P: 16 x ri blocks on the parent's locals (lcA + lcB)
-            for (int e = c_rowptr[leaf]; e < c_rowptr[leaf + 1]; e++) {
-                const C* U = cm + c_moff[e] + i;
-                const C* u = lcA + (size_t)c_col[e] * ldc;
-                const C* u2 = lcB ? lcB + (size_t)c_col[e] * ldc : nullptr;
-                const int ri = c_rin[e];
+    } else if (leaf < nleaf) {
+        const bool composed = grp == 1;
+        const int* rowptr = composed ? c_rowptr : l2p_rowptr;
+        if (rowptr != nullptr) {
+            for (int e = rowptr[leaf]; e < rowptr[leaf + 1]; e++) {
+                // composed: 16 x ri blocks on the parent level's locals (lcA + lcB); L2P: on the leaf's locals
+                const C* U = composed ? cm + c_moff[e] + i : l2p + l2p_moff[e] + i;
+                const C* u = composed ? lcA + (size_t)c_col[e] * ldc : lc + (size_t)leaf * ldl;
+                const C* u2 = composed ? (lcB ? lcB + (size_t)c_col[e] * ldc : nullptr) : (lc2 ? lc2 + (size_t)leaf * ldl : nullptr);
+                const int ri = composed ? c_rin[e] : l2p_rin[e];
+                // 16 columns at a time, unrolled so that every load issues before the first use
                 for (int j0 = 0; j0 < ri; j0 += 16) {
                     C uj[16], Uj[16];
 #pragma unroll
@@ -1199,31 +1203,19 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
                 }
             }
         }
-        if (grp == 2 && l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {
-            const int e = l2p_rowptr[leaf];
-            const C* U = l2p + l2p_moff[e] + i;
-            const C* u = lc + (size_t)leaf * ldl;
-            const C* u2 = lc2 ? lc2 + (size_t)leaf * ldl : nullptr;
-            const int ri = l2p_rin[e];
-            // 16 columns at a time, unrolled so that every load issues before the first use
-            for (int j0 = 0; j0 < ri; j0 += 16) {
-                C uj[16], Uj[16];
+    }
+    __syncthreads();
+    if (leaf < nleaf) {
+        const int l = leaf - q0;
 #pragma unroll
-                for (int j = 0; j < 16; j++)
-                    if (j0 + j < ri) {
-                        uj[j] = u[j0 + j];
-                        Uj[j] = U[(j0 + j) * 16];
-                        if (u2) {
-                            const C w = u2[j0 + j];
-                            uj[j].x += w.x;
-                            uj[j].y += w.y;
-                        }
-                    }
+        for (int sx = 0; sx < 3; sx++) {
+            const int o = grp * 3 + sx;  // offset (sx - 1, grp - 1); outside the domain vq holds zeros
+            const C* vs = vq[(1 + (l >> 1) + grp - 1) * 4 + 1 + (l & 1) + sx - 1];
+            const C* B = sn + o * 256 + i;
 #pragma unroll
-                for (int j = 0; j < 16; j += 2) {
-                    if (j0 + j < ri) cmac<T>(ar0, ai0, Uj[j], uj[j]);
-                    if (j0 + j + 1 < ri) cmac<T>(ar1, ai1, Uj[j + 1], uj[j + 1]);
-                }
+            for (int j = 0; j < 16; j += 2) {
+                cmac<T>(ar0, ai0, B[j * 16], vs[j]);
+                cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
             }
         }
     }
@@ -1236,8 +1228,7 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
         const C a = part[0][li], b = part[1][li];
         const T sr = mine.x + a.x + b.x, si = mine.y + a.y + b.y;
         const size_t gi = (size_t)leaf * 16 + i;
-        const double2 vv = v[gi];
-        const double sc = k2 * q[gi];
+        const double sc = k2 * qq;
         out[gi] = make_double2(vv.x + sc * (double)sr, vv.y + sc * (double)si);
     }
 }

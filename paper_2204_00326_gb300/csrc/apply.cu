@@ -874,19 +874,56 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
 // (broadcast across the 16 lanes of a half-warp) and the gathered input of
 // its right-hand side.  The operator is read once for all right-hand sides.
 constexpr int kRhsPerWarp = 16;
-constexpr int kMaxChunkColsB = kMaxChunkCols;  // gather buffer columns: every chunk record fits
-static_assert(kMaxChunkColsB >= kMaxChunkCols, "batched gather buffer smaller than a chunk");
+constexpr int kMaxChunkColsB = 64;  // columns of a chunk of the several-right-hand-side groups (input tile rows)
 
+// A stage holds a chunk's matrix and its input tile [column][rhs] (row stride nrhs_pad).
 template <typename T>
 struct BatchCfg {
     using C = typename V2<T>::t;
-    static constexpr int kStage = StreamCfg<T>::kStage;
+    static constexpr int kMat = StreamCfg<T>::kStage;
     __host__ __device__ static int xs_bytes(int nrhs_pad) { return kMaxChunkColsB * nrhs_pad * (int)sizeof(C); }
-    __host__ __device__ static int cta_bytes(int nrhs_pad) { return 2 * kStage + xs_bytes(nrhs_pad) + 128; }
+    __host__ __device__ static int stage_bytes(int nrhs_pad) { return kMat + xs_bytes(nrhs_pad); }
+    __host__ __device__ static int cta_bytes(int nrhs_pad) { return 2 * stage_bytes(nrhs_pad) + 128; }
 };
 
+// Start chunk c's copies into stage buffer st (matrix, then input tile) on
+// barrier bar: thread 0 arms the barrier for every byte and copies the
+// matrix; with bulk_x each input column (nrhs values, contiguous in x) is one
+// bulk copy by thread k of the CTA, else the block gathers the inputs itself
+// (synchronously, into the same tile).
+template <typename T>
+__device__ __forceinline__ void batch_issue(const GroupArgs<T>& g, const int4* recs, int c, unsigned char* st, unsigned long long* bar,
+                                            int nrhs, int nrhs_pad, bool bulk_x, int tid, int nthr)
+{
+    using C = typename V2<T>::t;
+    const int4 a = recs[2 * c], b = recs[2 * c + 1];
+    const PassArgs<T>& pa = g.p[a.x & 0xff];
+    const int ncol = a.z;
+    const unsigned xbytes = (unsigned)(nrhs * sizeof(C));
+    C* xt = (C*)(st + BatchCfg<T>::kMat);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        unsigned mbytes;
+        const char* src = chunk_src<T>(g, a, b, mbytes);
+        const unsigned total = mbytes + (bulk_x ? (unsigned)ncol * xbytes : 0u);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(total) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(st)),
+                     "l"(src), "r"(mbytes), "r"(smem_u32(bar))
+                     : "memory");
+    }
+    if (bulk_x) {
+        for (int k = tid; k < ncol; k += nthr) {
+            const C* src = pa.x + (size_t)pa.xmap[a.w + k] * nrhs;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             smem_u32(xt + (size_t)k * nrhs_pad)),
+                         "l"(src), "r"(xbytes), "r"(smem_u32(bar))
+                         : "memory");
+        }
+    }
+}
+
 template <typename T, int MR>
-__global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, int nrhs, int nrhs_pad, const int4* __restrict__ recs,
+__global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, int nrhs, int nrhs_pad, int bulk_x, const int4* __restrict__ recs,
                                                              const __grid_constant__ GroupArgs<T> g,
                                                              typename V2<T>::t* __restrict__ P, int Pld, int* __restrict__ cnt,
                                                              int* __restrict__ err)
@@ -895,9 +932,11 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    auto stage = [&](int k) { return (C*)(smem + (size_t)k * BatchCfg<T>::kStage); };
-    C* xs = (C*)(smem + 2 * BatchCfg<T>::kStage);
-    unsigned long long* bar = (unsigned long long*)(smem + 2 * BatchCfg<T>::kStage + BatchCfg<T>::xs_bytes(nrhs_pad));
+    const int sb = BatchCfg<T>::stage_bytes(nrhs_pad);
+    auto stage_raw = [&](int k) { return smem + (size_t)k * sb; };
+    auto stage = [&](int k) { return (C*)stage_raw(k); };
+    auto tile = [&](int k) { return (C*)(stage_raw(k) + BatchCfg<T>::kMat); };
+    unsigned long long* bar = (unsigned long long*)(smem + 2 * (size_t)sb);
     const int r = warp * kRhsPerWarp + (lane & 15);
     const int gsel = lane >> 4;
     const int cb = blockIdx.x * kpc;
@@ -907,13 +946,9 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int k = 0; k < 2 && cb + k < ce; k++) {
-            unsigned bytes;
-            const char* src = chunk_src<T>(g, recs[2 * (cb + k)], recs[2 * (cb + k) + 1], bytes);
-            tma_load(stage(k), src, bytes, &bar[k]);
-        }
     }
     __syncthreads();
+    for (int k = 0; k < 2 && cb + k < ce; k++) batch_issue<T>(g, recs, cb + k, stage_raw(k), &bar[k], nrhs, nrhs_pad, bulk_x, tid, blockDim.x);
     T ar[MR], ai[MR];
 #pragma unroll
     for (int m = 0; m < MR; m++) ar[m] = ai[m] = 0;
@@ -926,10 +961,13 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
         const int ro = (ra.x >> 16) & 0xffff;
         const int ld = ro + (ro & 1);
         const int ncol = ra.z;
-        // gather this chunk's inputs for every right-hand side: xs[k][rr]
-        for (int q = tid; q < ncol * nrhs; q += blockDim.x) {
-            const int k = q / nrhs, rr = q - k * nrhs;
-            xs[k * nrhs_pad + rr] = pa.x[(size_t)pa.xmap[ra.w + k] * nrhs + rr];
+        C* xs = tile(s);
+        if (!bulk_x) {
+            // gather this chunk's inputs for every right-hand side: xs[k][rr]
+            for (int q = tid; q < ncol * nrhs; q += blockDim.x) {
+                const int k = q / nrhs, rr = q - k * nrhs;
+                xs[k * nrhs_pad + rr] = pa.x[(size_t)pa.xmap[ra.w + k] * nrhs + rr];
+            }
         }
         const bool ok = __syncthreads_and(mbar_wait(&bar[s], parity));
         if (!ok) {
@@ -969,13 +1007,8 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
                 }
             }
         }
-        __syncthreads();  // everyone is done with this stage and the gather buffer
-        if (tid == 0 && c + 2 < ce) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            unsigned nbytes;
-            const char* src = chunk_src<T>(g, recs[2 * (c + 2)], recs[2 * (c + 2) + 1], nbytes);
-            tma_load(stage(s), src, nbytes, &bar[s]);
-        }
+        __syncthreads();  // everyone is done with this stage (matrix and inputs)
+        if (c + 2 < ce) batch_issue<T>(g, recs, c + 2, stage_raw(s), &bar[s], nrhs, nrhs_pad, bulk_x, tid, blockDim.x);
         const bool row_ends = (c + 1 == ce) || recs[2 * (c + 1)].x != ra.x || recs[2 * (c + 1)].y != ra.y;
         if (row_ends) {
             const bool direct = (ra.x & kFlagDirect) != 0;
@@ -1320,7 +1353,7 @@ struct PassCut {
     int pld = 0;
 };
 
-PassCut cut_pass(const BsrHost& b, int pass, int ldx, int accumulate, const std::vector<char>* initialized)
+PassCut cut_pass(const BsrHost& b, int pass, int ldx, int accumulate, const std::vector<char>* initialized, int max_cols = kMaxChunkCols)
 {
     PassCut pc;
     pc.rbase.assign(b.nrows, 0);
@@ -1338,7 +1371,7 @@ PassCut cut_pass(const BsrHost& b, int pass, int ldx, int accumulate, const std:
         pc.pld = std::max(pc.pld, ro);
         const int J = pc.cbase[r + 1] - pc.cbase[r];
         const int ldr = b.ld[r];
-        const int per = (int)std::max<long>(1, std::min<long>(kMaxChunkCols, kChunkElems / ldr));
+        const int per = (int)std::max<long>(1, std::min<long>(max_cols, kChunkElems / ldr));
         const int nck = (J + per - 1) / per;
         // add to y only where this application already wrote the row
         const int add = (accumulate && (!initialized || (*initialized)[r])) ? kFlagAddHost : 0;
@@ -1399,7 +1432,7 @@ void build_group(Group& g, const std::vector<PassRef>& passes, const std::vector
     std::vector<int4> recs;
     int pld = 0;
     for (size_t p = 0; p < hs.size(); p++) {
-        const PassCut pc = cut_pass(*hs[p], (int)p, ldx[p], accumulate, initialized);
+        const PassCut pc = cut_pass(*hs[p], (int)p, ldx[p], accumulate, initialized, kMaxChunkColsB);
         for (int r = 0; r < hs[p]->nrows; r++) place_row(recs, pc, r);
         pld = std::max(pld, pc.pld);
         upload_tables(g, pc);
@@ -1912,8 +1945,11 @@ void launch_batched_mr(const OpsDev& d, const Group& g, const GroupArgs<T>& ga, 
         const int ctas = std::max(1, std::min(g.nch, sms * per_sm));
         kpc = (g.nch + ctas - 1) / ctas;
         const int grid = (g.nch + kpc - 1) / kpc;
-        stream_batched_kernel<T, MR><<<(unsigned)grid, threads, smem, s>>>(g.nch, kpc, nrhs, nrhs_pad, g.chunks, ga, part, g.Pld,
-                                                                         g.cnt, d.err);
+        // inputs by bulk copies when every column is a 16-byte multiple at a 16-byte aligned address
+        int bulk_x = (nrhs * (int)sizeof(typename V2<T>::t)) % 16 == 0;
+        for (size_t p = 0; p < g.passes.size(); p++) bulk_x &= ((uintptr_t)ga.p[p].x % 16) == 0;
+        stream_batched_kernel<T, MR><<<(unsigned)grid, threads, smem, s>>>(g.nch, kpc, nrhs, nrhs_pad, bulk_x, g.chunks, ga, part,
+                                                                         g.Pld, g.cnt, d.err);
     }
 }
 

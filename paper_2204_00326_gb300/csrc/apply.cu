@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
 // (broadcast across the 16 lanes of a half-warp) and the gathered input of
 // its right-hand side.  The operator is read once for all right-hand sides.
 constexpr int kRhsPerWarp = 16;
-constexpr int kMaxChunkColsB = 64;  // columns of a chunk of the several-right-hand-side groups (input tile rows)
+constexpr int kMaxChunkColsB = 32;  // columns of a chunk of the several-right-hand-side groups (input tile rows)
 
 // A stage holds a chunk's matrix and its input tile [column][rhs] (row stride nrhs_pad).
 template <typename T>
@@ -919,6 +919,79 @@ __device__ __forceinline__ void batch_issue(const GroupArgs<T>& g, const int4* r
                          "l"(src), "r"(xbytes), "r"(smem_u32(bar))
                          : "memory");
         }
+    }
+}
+
+// acc[m] += M[m][k] x[k] over the chunk's columns for H rows of one lane (H
+// even, rows [i0, i0 + H) of a column of ld entries at M; x[k] at xs[k xst]).
+// Rows past the chunk's row count compute values that are never stored; their
+// reads stay inside the stage (the matrix is at most ld x ncol <= 1024 entries
+// and at most two rows past the last column are read, into the stage slack).
+// Columns are unrolled by U so that a lane with few rows still has about 16
+// independent products in flight between shared-memory loads.
+template <int H, int MR>
+__device__ __forceinline__ void batch_rows_h(float (&ar)[MR], float (&ai)[MR], const float2* M, const float2* xs, int ncol, int ld, int xst)
+{
+    constexpr int U = H >= 16 ? 1 : 16 / H;
+    int k = 0;
+    for (; k + U <= ncol; k += U) {
+        float2 xv[U];
+        float4 mm[U][H / 2];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            xv[u] = xs[(k + u) * xst];
+#pragma unroll
+            for (int m = 0; m < H / 2; m++) mm[u][m] = *(const float4*)(M + (k + u) * ld + 2 * m);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int m = 0; m < H / 2; m++) {
+                const float4 q = mm[u][m];
+                const float2 x = xv[u];
+                ar[2 * m] = fmaf(q.x, x.x, fmaf(-q.y, x.y, ar[2 * m]));
+                ai[2 * m] = fmaf(q.x, x.y, fmaf(q.y, x.x, ai[2 * m]));
+                ar[2 * m + 1] = fmaf(q.z, x.x, fmaf(-q.w, x.y, ar[2 * m + 1]));
+                ai[2 * m + 1] = fmaf(q.z, x.y, fmaf(q.w, x.x, ai[2 * m + 1]));
+            }
+    }
+    for (; k < ncol; k++) {
+        const float2 x = xs[k * xst];
+#pragma unroll
+        for (int m = 0; m < H / 2; m++) {
+            const float4 q = *(const float4*)(M + k * ld + 2 * m);
+            ar[2 * m] = fmaf(q.x, x.x, fmaf(-q.y, x.y, ar[2 * m]));
+            ai[2 * m] = fmaf(q.x, x.y, fmaf(q.y, x.x, ai[2 * m]));
+            ar[2 * m + 1] = fmaf(q.z, x.x, fmaf(-q.w, x.y, ar[2 * m + 1]));
+            ai[2 * m + 1] = fmaf(q.z, x.y, fmaf(q.w, x.x, ai[2 * m + 1]));
+        }
+    }
+}
+
+template <int H, int MR>
+__device__ __forceinline__ void batch_rows_h(double (&ar)[MR], double (&ai)[MR], const double2* M, const double2* xs, int ncol, int ld, int xst)
+{
+    for (int k = 0; k < ncol; k++) {
+        const double2 x = xs[k * xst];
+#pragma unroll
+        for (int m = 0; m < H; m++) {
+            const double2 q = M[k * ld + m];
+            ar[m] = fma(q.x, x.x, fma(-q.y, x.y, ar[m]));
+            ai[m] = fma(q.x, x.y, fma(q.y, x.x, ai[m]));
+        }
+    }
+}
+
+// Dispatch on the lane's row count h (even, at most MR; uniform over the CTA).
+template <typename T, int MR, int H = 2>
+__device__ __forceinline__ void batch_rows(int h, T (&ar)[MR], T (&ai)[MR], const typename V2<T>::t* M, const typename V2<T>::t* xs, int ncol,
+                                           int ld, int xst)
+{
+    if constexpr (H <= MR) {
+        if (h == H)
+            batch_rows_h<H, MR>(ar, ai, M, xs, ncol, ld, xst);
+        else
+            batch_rows<T, MR, H + 2>(h, ar, ai, M, xs, ncol, ld, xst);
     }
 }
 
@@ -982,31 +1055,7 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
         // rows of this lane: [gsel h, gsel h + h), h even
         const int h = ((ro + 3) >> 2) << 1;
         const int i0 = gsel * h;
-        const C* M = stage(s) + i0;
-        if (r < nrhs) {
-            for (int k = 0; k < ncol; k++) {
-                const C xv = xs[k * nrhs_pad + r];
-                const C* Mk = M + k * ld;
-#pragma unroll
-                for (int m = 0; m < MR; m += 2) {
-                    if (m < h && i0 + m < ro) {
-                        if constexpr (sizeof(T) == 4) {
-                            const float4 mm = *(const float4*)(Mk + m);
-                            ar[m] = fmaf(mm.x, xv.x, fmaf(-mm.y, xv.y, ar[m]));
-                            ai[m] = fmaf(mm.x, xv.y, fmaf(mm.y, xv.x, ai[m]));
-                            ar[m + 1] = fmaf(mm.z, xv.x, fmaf(-mm.w, xv.y, ar[m + 1]));
-                            ai[m + 1] = fmaf(mm.z, xv.y, fmaf(mm.w, xv.x, ai[m + 1]));
-                        } else {
-                            const C m0 = Mk[m], m1 = Mk[m + 1];
-                            ar[m] = fma(m0.x, xv.x, fma(-m0.y, xv.y, ar[m]));
-                            ai[m] = fma(m0.x, xv.y, fma(m0.y, xv.x, ai[m]));
-                            ar[m + 1] = fma(m1.x, xv.x, fma(-m1.y, xv.y, ar[m + 1]));
-                            ai[m + 1] = fma(m1.x, xv.y, fma(m1.y, xv.x, ai[m + 1]));
-                        }
-                    }
-                }
-            }
-        }
+        if (r < nrhs) batch_rows<T, MR>(h, ar, ai, stage(s) + i0, xs + r, ncol, ld, nrhs_pad);
         __syncthreads();  // everyone is done with this stage (matrix and inputs)
         if (c + 2 < ce) batch_issue<T>(g, recs, c + 2, stage_raw(s), &bar[s], nrhs, nrhs_pad, bulk_x, tid, blockDim.x);
         const bool row_ends = (c + 1 == ce) || recs[2 * (c + 1)].x != ra.x || recs[2 * (c + 1)].y != ra.y;

@@ -414,29 +414,53 @@ __device__ __forceinline__ void chunk_mac(Acc<T>& acc, const typename V2<T>::t* 
         }
     } else {
         if (ro <= 32) {
+            // four column streams per lane (sets 0/1, slots 0/1); slot 1 is
+            // folded into slot 0 at the end, so it is zero between calls
             const int JP = 32 / ro, i = lane % ro, jp = lane / ro;
             if (jp >= JP) return;
             const double2* Mi = M + i;
             int j = jp;
-#pragma unroll 2
-            for (; j + JP < ncol; j += 2 * JP) {
-                const double2 m0 = Mi[j * ld], m1 = Mi[(j + JP) * ld];
-                const double2 x0 = xs[j], x1 = xs[j + JP];
+            for (; j + 3 * JP < ncol; j += 4 * JP) {
+                const double2 m0 = Mi[j * ld], m1 = Mi[(j + JP) * ld], m2 = Mi[(j + 2 * JP) * ld], m3 = Mi[(j + 3 * JP) * ld];
+                const double2 x0 = xs[j], x1 = xs[j + JP], x2 = xs[j + 2 * JP], x3 = xs[j + 3 * JP];
                 acc.r[0][0] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][0]));
                 acc.i[0][0] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][0]));
                 acc.r[1][0] = fma(m1.x, x1.x, fma(-m1.y, x1.y, acc.r[1][0]));
                 acc.i[1][0] = fma(m1.x, x1.y, fma(m1.y, x1.x, acc.i[1][0]));
+                acc.r[0][1] = fma(m2.x, x2.x, fma(-m2.y, x2.y, acc.r[0][1]));
+                acc.i[0][1] = fma(m2.x, x2.y, fma(m2.y, x2.x, acc.i[0][1]));
+                acc.r[1][1] = fma(m3.x, x3.x, fma(-m3.y, x3.y, acc.r[1][1]));
+                acc.i[1][1] = fma(m3.x, x3.y, fma(m3.y, x3.x, acc.i[1][1]));
             }
-            if (j < ncol) {
+            for (; j < ncol; j += JP) {
                 const double2 m0 = Mi[j * ld];
                 const double2 x0 = xs[j];
                 acc.r[0][0] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][0]));
                 acc.i[0][0] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][0]));
             }
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                acc.r[s][0] += acc.r[s][1];
+                acc.i[s][0] += acc.i[s][1];
+                acc.r[s][1] = acc.i[s][1] = 0;
+            }
         } else {
+            // rows lane + 32 k; even columns into set 0, odd into set 1
             const int nck = (ro + 31) / 32;
-#pragma unroll 2
-            for (int j = 0; j < ncol; j++) {
+            int j = 0;
+            for (; j + 1 < ncol; j += 2) {
+                const double2 x0 = xs[j], x1 = xs[j + 1];
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (k < nck && k * 32 + lane < ro) {
+                        const double2 m0 = M[j * ld + k * 32 + lane], m1 = M[(j + 1) * ld + k * 32 + lane];
+                        acc.r[0][k] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][k]));
+                        acc.i[0][k] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][k]));
+                        acc.r[1][k] = fma(m1.x, x1.x, fma(-m1.y, x1.y, acc.r[1][k]));
+                        acc.i[1][k] = fma(m1.x, x1.y, fma(m1.y, x1.x, acc.i[1][k]));
+                    }
+            }
+            if (j < ncol) {
                 const double2 x0 = xs[j];
 #pragma unroll
                 for (int k = 0; k < 4; k++)

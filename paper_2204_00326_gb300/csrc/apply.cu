@@ -48,7 +48,8 @@ constexpr int kMaxPhase = 32;       // phases of the fused single-right-hand-sid
 constexpr int kMaxRhs = 64;         // right-hand sides of one application
 constexpr int kFlagDirectHost = 1 << 8;  // same bits as the device-side record flags
 constexpr int kFlagAddHost = 1 << 9;
-constexpr long kChunkElems = 1024;  // matrix entries per chunk (8 KB in complex64)
+constexpr long kChunkElems = 1024;    // matrix entries per chunk (8 KB in complex64)
+constexpr long kChunkElems64 = 512;   // per chunk of the single-right-hand-side complex128 launch (8 KB)
 
 template <typename T>
 struct PassArgs {
@@ -101,7 +102,9 @@ constexpr long kSpinLimit = 1L << 22;  // bounded mbarrier waits
 template <typename T>
 struct StreamCfg {
     using C = typename V2<T>::t;
-    static constexpr int kStage = ((int)(kChunkElems * sizeof(C)) + 32 + 127) / 128 * 128;
+    // complex128 chunks hold half as many entries, so that three CTAs fit an SM
+    static constexpr long kElems = sizeof(T) == 8 ? kChunkElems64 : kChunkElems;
+    static constexpr int kStage = ((int)(kElems * sizeof(C)) + 32 + 127) / 128 * 128;
     static constexpr int kXs = kMaxChunkCols * (int)sizeof(C);
     static constexpr int kWarp = 2 * kStage + kXs + 128;  // two stages, gather buffer, barriers
     static constexpr int kCta = kStreamWarps * kWarp;
@@ -904,7 +907,7 @@ constexpr int kMaxChunkColsB = 32;  // columns of a chunk of the several-right-h
 template <typename T>
 struct BatchCfg {
     using C = typename V2<T>::t;
-    static constexpr int kMat = StreamCfg<T>::kStage;
+    static constexpr int kMat = ((int)(kChunkElems * sizeof(C)) + 32 + 127) / 128 * 128;
     __host__ __device__ static int xs_bytes(int nrhs_pad) { return kMaxChunkColsB * nrhs_pad * (int)sizeof(C); }
     __host__ __device__ static int stage_bytes(int nrhs_pad) { return kMat + xs_bytes(nrhs_pad); }
     __host__ __device__ static int cta_bytes(int nrhs_pad) { return 2 * stage_bytes(nrhs_pad) + 128; }
@@ -1426,7 +1429,8 @@ struct PassCut {
     int pld = 0;
 };
 
-PassCut cut_pass(const BsrHost& b, int pass, int ldx, int accumulate, const std::vector<char>* initialized, int max_cols = kMaxChunkCols)
+PassCut cut_pass(const BsrHost& b, int pass, int ldx, int accumulate, const std::vector<char>* initialized, int max_cols = kMaxChunkCols,
+                 long max_elems = kChunkElems)
 {
     PassCut pc;
     pc.rbase.assign(b.nrows, 0);
@@ -1444,7 +1448,7 @@ PassCut cut_pass(const BsrHost& b, int pass, int ldx, int accumulate, const std:
         pc.pld = std::max(pc.pld, ro);
         const int J = pc.cbase[r + 1] - pc.cbase[r];
         const int ldr = b.ld[r];
-        const int per = (int)std::max<long>(1, std::min<long>(max_cols, kChunkElems / ldr));
+        const int per = (int)std::max<long>(1, std::min<long>(max_cols, max_elems / ldr));
         const int nck = (J + per - 1) / per;
         // add to y only where this application already wrote the row
         const int add = (accumulate && (!initialized || (*initialized)[r])) ? kFlagAddHost : 0;
@@ -1663,12 +1667,16 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
     }
     const int np = (int)passes.size();
     if (np > kMaxPass) fail(DAFMM_EBADARG, "too many far-field levels for the fused launch");
-    std::vector<PassCut> cuts;
+    // chunk records of plan 0 (complex128) and plan 1 (complex64); the row and
+    // column tables do not depend on the chunk size
+    std::vector<PassCut> cuts_k[2];
     int pld = 0;
     for (int p = 0; p < np; p++) {
-        cuts.push_back(cut_pass(*hs[p], p, ldx[p], 0, nullptr));
-        pld = std::max(pld, cuts[p].pld);
+        cuts_k[0].push_back(cut_pass(*hs[p], p, ldx[p], 0, nullptr, kMaxChunkCols, StreamCfg<double>::kElems));
+        cuts_k[1].push_back(cut_pass(*hs[p], p, ldx[p], 0, nullptr, kMaxChunkCols, StreamCfg<float>::kElems));
+        pld = std::max(pld, cuts_k[1][p].pld);
     }
+    const std::vector<PassCut>& cuts = cuts_k[1];
     std::vector<int> asap(np, 0), alap(np, 0);
     for (int p = 0; p < np; p++)
         for (int q = 0; q < p; q++)
@@ -1681,7 +1689,8 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
         for (int r = p + 1; r < np; r++)
             if (deps[r] >> p & 1u) alap[p] = std::min(alap[p], asap[r] - 1);
     }
-    auto chunks = [&](int p, int r) { return cuts[p].first[r + 1] - cuts[p].first[r]; };
+    auto chunks_in = [&](int k, int p, int r) { return cuts_k[k][p].first[r + 1] - cuts_k[k][p].first[r]; };
+    auto chunks = [&](int p, int r) { return chunks_in(1, p, r); };
     std::vector<char> slack(np, 0);
     for (int p = 0; p < np; p++) slack[p] = alap[p] > asap[p];
     F.dphase.assign(np, -1);
@@ -1695,6 +1704,8 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
     for (int k = 0; k < 2; k++) {
         FusedPlan& P = F.plan[k];
         const bool dynamic = k == 0;
+        auto chunks = [&](int p, int r) { return chunks_in(k, p, r); };
+        const std::vector<PassCut>& cuts = cuts_k[k];
         // rows of every phase: the chain at its phase; in the static plan the
         // slack rows fill each phase up to about one chunk per warp (more would
         // take bandwidth from the chain), the rest going to the earliest

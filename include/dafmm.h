@@ -258,13 +258,45 @@ int hodlr_factor(const dafmm_ops* ops, int rank, double tol, int leaf_size, dafm
 
 /*
  * hodlr_solve -- x = A~^{-1} b for one right-hand side (nrhs must be 1):
- * batched leaf inverses, then per level from the leaves up t = W x, s =
- * S^{-1} t, x -= Ut s.  Cost O(r N log N).  b_dev, x_dev: N complex128 on
- * the device; x_dev == b_dev is allowed.  precision: DAFMM_FP64, or
- * DAFMM_MIXED (complex64 factors and arithmetic, complex128 boundary
- * vectors).  Asynchronous on stream.
+ * leaf inverses, then per level from the leaves up t = W x, s = S^{-1} t,
+ * x -= Ut s (recursive Sherman-Morrison-Woodbury, Section 6).  Cost
+ * O(r N log N).  One cooperative launch whose CTAs meet at a grid barrier
+ * per level; each barrier wait has a limit (about 0.2 s), after which the
+ * launch sets the handle's error flag and returns (see hodlr_sync).
+ * b_dev, x_dev: N complex128 on the device; x_dev == b_dev is allowed.
+ * precision: DAFMM_FP64, or DAFMM_MIXED (complex64 factors and arithmetic,
+ * complex128 boundary vectors).  Asynchronous on stream.  Calls on one
+ * handle must be ordered (one stream): they share work buffers.
  */
 int hodlr_solve(const dafmm_hodlr* M, int nrhs, const double* b_dev, double* x_dev, int precision, void* stream);
+
+/*
+ * hodlr_sync -- synchronise the stream, then report whether an application
+ * on this handle gave up a barrier wait since the last check
+ * (DAFMM_ETIMEOUT; the flag is cleared and the barrier re-armed; the result
+ * of that application is undefined).  gmres_solve checks this itself.
+ * Errors: DAFMM_EBADARG for NULL, DAFMM_ECUDA.
+ */
+int hodlr_sync(const dafmm_hodlr* M, void* stream);
+
+/*
+ * hodlr_set_ctas -- width of the hodlr_solve launch (CTAs; each owns N / ctas
+ * consecutive unknowns).  0 restores the width chosen at factorisation (a
+ * power of two, all CTAs resident at once, at most one per leaf, about 2048
+ * unknowns per CTA on large problems and at least 128 CTAs).  Otherwise ctas
+ * must be a power of two, at most N / leaf_size and at most the number of
+ * CTAs the device holds at once.  A tuning and test knob; the result does
+ * not depend on it beyond rounding.  Errors: DAFMM_EBADARG.
+ */
+int hodlr_set_ctas(dafmm_hodlr* M, int ctas);
+
+/*
+ * hodlr_debug_stall -- test support for the timeout path (the paper has no
+ * counterpart): the next hodlr_solve on this handle waits at its first grid
+ * barrier for one CTA more than the launch has, so every wait gives up and
+ * hodlr_sync returns DAFMM_ETIMEOUT.  Errors: DAFMM_EBADARG for NULL.
+ */
+int hodlr_debug_stall(const dafmm_hodlr* M);
 
 /*
  * hodlr_export -- the dense N x N matrix A~ assembled from the factors

@@ -2267,6 +2267,8 @@ void profile_read(OpsDev& d, dafmm_profile_t& p)
 
 void free_ops(OpsDev& d)
 {
+    gmres_work_free(d.gw);
+    d.gw = nullptr;
     for (cudaEvent_t e : d.events) cudaEventDestroy(e);
     d.events.clear();
     for (auto& row : d.gc)

@@ -315,6 +315,8 @@ int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, const double* f, double* x
             prec = hodlr_prec;
         }
         code = gmres_run(ops->tree->t, ops->dev, M, prec, f, x, *opts, *st, (cudaStream_t)stream);
+        if (M && hodlr_check(M, (cudaStream_t)stream) == DAFMM_ETIMEOUT)
+            fail(DAFMM_ETIMEOUT, "a wait of the HODLR application gave up; the solution is undefined");
         if (code == DAFMM_ENOTCONV)
             fail(DAFMM_ENOTCONV, "GMRES reached max_iters at relative residual " + std::to_string(st->rel_residual));
     });
@@ -338,6 +340,31 @@ int hodlr_solve(const dafmm_hodlr* M, int nrhs, const double* b, double* x, int 
         if (nrhs != 1) fail(DAFMM_EBADARG, "hodlr_solve applies one right-hand side per call");
         if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
         hodlr_apply(M, b, x, precision, (cudaStream_t)stream);
+    });
+}
+
+int hodlr_sync(const dafmm_hodlr* M, void* stream)
+{
+    return guarded([&] {
+        if (!M) fail(DAFMM_EBADARG, "NULL argument");
+        if (hodlr_check(M, (cudaStream_t)stream) == DAFMM_ETIMEOUT)
+            fail(DAFMM_ETIMEOUT, "a grid barrier of the HODLR application gave up");
+    });
+}
+
+int hodlr_set_ctas(dafmm_hodlr* M, int ctas)
+{
+    return guarded([&] {
+        if (!M) fail(DAFMM_EBADARG, "NULL argument");
+        hodlr_set_width(M, ctas);
+    });
+}
+
+int hodlr_debug_stall(const dafmm_hodlr* M)
+{
+    return guarded([&] {
+        if (!M) fail(DAFMM_EBADARG, "NULL argument");
+        hodlr_set_stall(M, 1);
     });
 }
 
@@ -560,6 +587,8 @@ int gmres_solve_learned(dafmm_ops* ops, const dafmm_hodlr* M, dafmm_unet* net, i
         } else {
             code = gmres_run(t, ops->dev, M, M ? hodlr_prec : nullptr, f, x, *opts, *st, s);
         }
+        if (M && hodlr_check(M, s) == DAFMM_ETIMEOUT)
+            fail(DAFMM_ETIMEOUT, "a wait of the HODLR application gave up; the solution is undefined");
         if (code == DAFMM_ENOTCONV)
             fail(DAFMM_ENOTCONV, "GMRES reached max_iters at relative residual " + std::to_string(st->rel_residual));
     });

@@ -12,9 +12,15 @@
 // correction equations are solved to a relative inner tolerance.
 //
 // Arnoldi (classical Gram-Schmidt applied twice), the Hessenberg matrix, the
-// Givens rotations and every vector update stay in FP64 on the device; the
-// host reads one residual estimate (8 bytes) per inner iteration to decide
-// when to stop.  Dot products use two-phase (deterministic) reductions.
+// Givens rotations and every vector update stay in FP64 on the device.  One
+// Arnoldi step is three reduction kernels (the last block of each sums the
+// per-block partials in block order, so results do not depend on timing) and
+// a scaling; the host reads one residual estimate (8 bytes) per step to
+// decide when to stop.  While it waits for step j it may already have queued
+// step j + 1 when the estimates so far predict that step j misses the target
+// by far (geometric extrapolation); a step queued that way and not needed
+// writes only columns the final update does not read.  A zero initial guess
+// takes r = f without an application.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,7 +43,9 @@ namespace {
         }                                                                                         \
     } while (0)
 
-constexpr int kRowBlock = 2048;  // rows per partial of a dot product
+constexpr int kAT = 256;  // threads per block of the reduction kernels
+constexpr int kCR = 64;   // rows per block: the block stages V[rows, 0..nk) in shared memory
+constexpr int kMaxM = 128;
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -46,78 +54,244 @@ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b)  // conj(a) * 
     return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
-// part[k][rb] = sum_{i in block rb} conj(V[i, k]) w[i], k < nk.
-__global__ void __launch_bounds__(kThreads) dots_partial_kernel(long N, const double2* __restrict__ V, long ldv, int nk,
-                                                                const double2* __restrict__ w, double2* __restrict__ part, int nrb)
+// True in the last block of the grid to get here (its partials and everyone
+// else's are visible to it); that block re-arms the ticket.
+__device__ bool last_block(unsigned* ticket)
 {
-    __shared__ double2 sh[kThreads / 32];
-    const int rb = blockIdx.x, k = blockIdx.y;
-    const long i0 = (long)rb * kRowBlock;
-    const long i1 = min(N, i0 + kRowBlock);
-    const double2* v = V + (size_t)k * ldv;
-    double sr = 0, si = 0;
-    for (long i = i0 + threadIdx.x; i < i1; i += kThreads) {
-        const double2 p = cconjmul(v[i], w[i]);
-        sr += p.x;
-        si += p.y;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_down_sync(0xffffffffu, sr, o);
-        si += __shfl_down_sync(0xffffffffu, si, o);
-    }
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_double2(sr, si);
+    __shared__ int s_last;
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        double2 t = make_double2(0, 0);
-        for (int q = 0; q < kThreads / 32; q++) {
-            t.x += sh[q].x;
-            t.y += sh[q].y;
-        }
-        part[(size_t)k * nrb + rb] = t;
+        const int last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (last) *ticket = 0;
+        s_last = last;
     }
-}
-
-// out[k] (+)= sum_rb part[k][rb] for k < nk, in block order.
-__global__ void dots_final_kernel(int nk, int nrb, const double2* __restrict__ part, double2* __restrict__ out, int accumulate)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nk) return;
-    double2 t = accumulate ? out[k] : make_double2(0, 0);
-    for (int rb = 0; rb < nrb; rb++) {
-        t.x += part[(size_t)k * nrb + rb].x;
-        t.y += part[(size_t)k * nrb + rb].y;
-    }
-    out[k] = t;
-}
-
-// w[i] -= sum_{k<nk} V[i, k] h[k]
-__global__ void __launch_bounds__(kThreads) sub_vh_kernel(long N, const double2* __restrict__ V, long ldv, int nk,
-                                                          const double2* __restrict__ h, double2* __restrict__ w)
-{
-    __shared__ double2 hs[128];
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = h[k];
     __syncthreads();
-    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double2 a = w[i];
-    for (int k = 0; k < nk; k++) {
-        const double2 p = cmul(V[(size_t)k * ldv + i], hs[k]);
-        a.x -= p.x;
-        a.y -= p.y;
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// Vs[k][r] = V[r0 + r, k] for r < rows, k < nk, by 16-byte asynchronous copies
+// (all in flight at once), then wait.
+__device__ __forceinline__ void stage_tile(const double2* __restrict__ V, long N, int nk, long r0, int rows, double2* Vs)
+{
+    for (int e = threadIdx.x; e < nk * kCR; e += blockDim.x) {
+        const int k = e / kCR, r = e - k * kCR;
+        if (r < rows) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(Vs + e);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(V + (size_t)k * N + r0 + r) : "memory");
+        }
     }
-    w[i] = a;
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+}
+
+// ws[r] = w[r0 + r] - sum_k Vs[k][r] h[k] (h == nullptr: no update), four
+// threads per row splitting k; rows past the end are zero.  Writes the
+// updated rows back to w when h is given.
+__device__ __forceinline__ void tile_update(const double2* Vs, int nk, const double2* hs, double2* __restrict__ w, long r0, int rows,
+                                            double2* ws)
+{
+    const int r = threadIdx.x >> 2, part = threadIdx.x & 3;  // kAT = 4 kCR
+    double2 a = make_double2(0, 0);
+    if (hs)
+        for (int k = part; k < nk; k += 4) {
+            const double2 p = cmul(Vs[k * kCR + r], hs[k]);
+            a.x += p.x;
+            a.y += p.y;
+        }
+    for (int o = 1; o < 4; o <<= 1) {
+        a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+        a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+    }
+    if (part == 0) {
+        double2 v = make_double2(0, 0);
+        if (r < rows) {
+            v = w[r0 + r];
+            v.x -= a.x;
+            v.y -= a.y;
+            if (hs) w[r0 + r] = v;
+        }
+        ws[r] = v;
+    }
+    __syncthreads();
+}
+
+// Sum over blocks of part[k][*] for k < nk into out (last block, warp per k).
+__device__ __forceinline__ void reduce_blocks(const double2* part, int nk, int nrb, double2* out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kW = kAT / 32;
+    for (int k0 = warp; k0 < nk; k0 += 2 * kW) {
+        double2 t[2] = {make_double2(0, 0), make_double2(0, 0)};
+#pragma unroll 8
+        for (int rb = lane; rb < nrb; rb += 32)
+#pragma unroll
+            for (int u = 0; u < 2; u++)
+                if (k0 + u * kW < nk) {
+                    const double2 p = __ldcg(&part[(size_t)(k0 + u * kW) * nrb + rb]);
+                    t[u].x += p.x;
+                    t[u].y += p.y;
+                }
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                t[u].x += __shfl_xor_sync(0xffffffffu, t[u].x, o);
+                t[u].y += __shfl_xor_sync(0xffffffffu, t[u].y, o);
+            }
+        if (lane < 2 && k0 + lane * kW < nk) out[k0 + lane * kW] = lane ? t[1] : t[0];
+    }
+}
+
+// out[0..nk) = V[:, 0..nk)^H w, after w -= V h_in when h_in is given.
+// Dynamic shared memory: nk kCR complex128.  part: nk x gridDim.x partials.
+__global__ void __launch_bounds__(kAT) cgs_kernel(long N, const double2* __restrict__ V, int nk, const double2* __restrict__ h_in,
+                                                  double2* __restrict__ w, double2* __restrict__ part, unsigned* ticket,
+                                                  double2* __restrict__ out)
+{
+    extern __shared__ double2 Vs[];
+    __shared__ double2 hs[kMaxM + 1];
+    __shared__ double2 ws[kCR];
+    const long r0 = (long)blockIdx.x * kCR;
+    const int rows = (int)min((long)kCR, N - r0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nrb = gridDim.x;
+    if (h_in)
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = h_in[k];
+    stage_tile(V, N, nk, r0, rows, Vs);
+    tile_update(Vs, nk, h_in ? hs : nullptr, w, r0, rows, ws);
+    // column k by warp k % 8, lanes over the rows
+    for (int k = warp; k < nk; k += kAT / 32) {
+        double2 p = make_double2(0, 0);
+        for (int r = lane; r < kCR; r += 32) {
+            const double2 q = cconjmul(Vs[k * kCR + r], ws[r]);
+            p.x += r < rows ? q.x : 0.0;
+            p.y += r < rows ? q.y : 0.0;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            p.x += __shfl_xor_sync(0xffffffffu, p.x, o);
+            p.y += __shfl_xor_sync(0xffffffffu, p.y, o);
+        }
+        if (lane == 0) part[(size_t)k * nrb + blockIdx.x] = p;
+    }
+    if (!last_block(ticket)) return;
+    reduce_blocks(part, nk, nrb, out);
+}
+
+// Givens bookkeeping for column j by one warp: h[0..j] = h1 + h2, h[j+1] =
+// |w| and the previous rotations are staged in shared memory by the warp;
+// lane 0 applies the rotations (they chain), forms the new one, updates g
+// and publishes |g[j+1]| (the residual norm of the least-squares problem);
+// the warp writes the column back.  H is (m+1) x m column-major.
+__device__ void givens_step(int j, int m, const double2* h1, const double2* h2, double wn2, double2* H, double2* cs, double2* sn, double2* g,
+                            double* res)
+{
+    __shared__ double2 col[kMaxM + 1], ss[kMaxM];
+    __shared__ double cc[kMaxM];
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k <= j; k += 32) col[k] = make_double2(__ldcg(&h1[k]).x + __ldcg(&h2[k]).x, __ldcg(&h1[k]).y + __ldcg(&h2[k]).y);
+    for (int k = lane; k < j; k += 32) {
+        cc[k] = cs[k].x;
+        ss[k] = sn[k];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        col[j + 1] = make_double2(sqrt(wn2), 0.0);
+        // previous rotations: [c s; -conj(s) c] with real c
+        for (int k = 0; k < j; k++) {
+            const double c = cc[k];
+            const double2 s = ss[k];
+            const double2 a = col[k], b = col[k + 1];
+            const double2 sb = cmul(s, b);
+            const double2 csa = make_double2(s.x * a.x + s.y * a.y, s.x * a.y - s.y * a.x);  // conj(s) a
+            col[k] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
+            col[k + 1] = make_double2(-csa.x + c * b.x, -csa.y + c * b.y);
+        }
+        // new rotation zeroing col[j+1]
+        const double2 a = col[j], b = col[j + 1];
+        const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
+        double c;
+        double2 s;
+        if (nb == 0.0) {
+            c = 1.0;
+            s = make_double2(0, 0);
+        } else if (na == 0.0) {
+            c = 0.0;
+            s = make_double2(b.x / nb, -b.y / nb);  // conj(b)/|b|
+        } else {
+            const double t = hypot(na, nb);
+            c = na / t;
+            const double2 ua = make_double2(a.x / na, a.y / na);  // a/|a|
+            // s = (a/|a|) conj(b) / t
+            s = make_double2((ua.x * b.x + ua.y * b.y) / t, (ua.y * b.x - ua.x * b.y) / t);
+        }
+        cs[j] = make_double2(c, 0.0);
+        sn[j] = s;
+        const double2 sb = cmul(s, b);
+        col[j] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
+        col[j + 1] = make_double2(0.0, 0.0);
+        const double2 gj = g[j];
+        const double2 csg = make_double2(s.x * gj.x + s.y * gj.y, s.x * gj.y - s.y * gj.x);  // conj(s) g_j
+        g[j] = make_double2(c * gj.x, c * gj.y);
+        g[j + 1] = make_double2(-csg.x, -csg.y);
+        *res = hypot(g[j + 1].x, g[j + 1].y);
+    }
+    __syncwarp();
+    double2* hc = H + (size_t)j * (m + 1);
+    for (int k = lane; k <= j + 1; k += 32) hc[k] = col[k];
+}
+
+struct GivensArgs {
+    int j, m;
+    const double2 *h1, *h2;
+    double2 *H, *cs, *sn, *g;
+    double* res;
+};
+
+// w -= V h_in (h_in may be null), then |w|^2 -> *wn2 (real part); with
+// gv.H, the last block also takes the Givens step of column gv.j.
+// Dynamic shared memory: nk kCR complex128.  part: gridDim.x partials.
+__global__ void __launch_bounds__(kAT) cgs_norm_kernel(long N, const double2* __restrict__ V, int nk, const double2* __restrict__ h_in,
+                                                       double2* __restrict__ w, double2* __restrict__ part, unsigned* ticket,
+                                                       double2* __restrict__ wn2, GivensArgs gv)
+{
+    extern __shared__ double2 Vs[];
+    __shared__ double2 hs[kMaxM + 1];
+    __shared__ double2 ws[kCR];
+    const long r0 = (long)blockIdx.x * kCR;
+    const int rows = (int)min((long)kCR, N - r0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nrb = gridDim.x;
+    if (h_in)
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = h_in[k];
+    if (h_in) stage_tile(V, N, nk, r0, rows, Vs);
+    tile_update(Vs, h_in ? nk : 0, h_in ? hs : nullptr, w, r0, rows, ws);
+    if (warp == 0) {
+        double s2 = 0;
+        for (int r = lane; r < kCR; r += 32) s2 += ws[r].x * ws[r].x + ws[r].y * ws[r].y;
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) part[blockIdx.x] = make_double2(s2, 0.0);
+    }
+    if (!last_block(ticket)) return;
+    if (warp == 0) {
+        double t = 0;
+#pragma unroll 8
+        for (int rb = lane; rb < nrb; rb += 32) t += __ldcg(&part[rb]).x;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) *wn2 = make_double2(t, 0.0);
+        if (gv.H) givens_step(gv.j, gv.m, gv.h1, gv.h2, t, gv.H, gv.cs, gv.sn, gv.g, gv.res);
+    }
 }
 
 // x[i] += sum_{k<nk} Z[i, k] y[k]
 __global__ void __launch_bounds__(kThreads) add_zy_kernel(long N, const double2* __restrict__ Z, long ldz, int nk,
                                                           const double2* __restrict__ y, double2* __restrict__ x)
 {
-    __shared__ double2 ys[128];
+    __shared__ double2 ys[kMaxM];
     for (int k = threadIdx.x; k < nk; k += blockDim.x) ys[k] = y[k];
     __syncthreads();
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double2 a = x[i];
+#pragma unroll 8
     for (int k = 0; k < nk; k++) {
         const double2 p = cmul(Z[(size_t)k * ldz + i], ys[k]);
         a.x += p.x;
@@ -126,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) add_zy_kernel(long N, const double2*
     x[i] = a;
 }
 
-// out = a * s where s = 1 / sqrt(re(*nrm2)) (scale by the inverse norm), or out = a - b.
+// out = a / sqrt(re(*nrm2)) (0 when the norm is 0)
 __global__ void scale_inv_norm_kernel(long N, const double2* __restrict__ a, const double2* __restrict__ nrm2, double2* __restrict__ out)
 {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -143,72 +317,30 @@ __global__ void sub_kernel(long N, const double2* __restrict__ a, const double2*
     out[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
 }
 
-// Arnoldi bookkeeping for column j (one thread): h[0..j] from the two Gram-
-// Schmidt passes, h[j+1] = |w|; apply the previous rotations, form the new
-// one, update g and publish |g[j+1]| (the residual norm of the least-squares
-// problem).  H is (m+1) x m column-major.
-__global__ void givens_kernel(int j, int m, const double2* __restrict__ h1, const double2* __restrict__ h2,
-                              const double2* __restrict__ wn2, double2* __restrict__ H, double2* __restrict__ cs,
-                              double2* __restrict__ sn, double2* __restrict__ g, double* __restrict__ res)
+// Back substitution H[0:n,0:n] y = g[0:n], one block of kMaxM threads:
+// thread t keeps g[t]; for i from n-1 down, y[i] = g[i] / H[i][i], then every
+// t < i subtracts H[t][i] y[i] (column i of H is contiguous).
+__global__ void __launch_bounds__(kMaxM) backsolve_kernel(int n, int m, const double2* __restrict__ H, const double2* __restrict__ g,
+                                                          double2* __restrict__ y)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double2* col = H + (size_t)j * (m + 1);
-    for (int k = 0; k <= j; k++) col[k] = make_double2(h1[k].x + h2[k].x, h1[k].y + h2[k].y);
-    col[j + 1] = make_double2(sqrt(wn2->x), 0.0);
-    // previous rotations: [c s; -conj(s) c] with real c
-    for (int k = 0; k < j; k++) {
-        const double c = cs[k].x;
-        const double2 s = sn[k];
-        const double2 a = col[k], b = col[k + 1];
-        const double2 sb = cmul(s, b);
-        const double2 csa = make_double2(s.x * a.x + s.y * a.y, s.x * a.y - s.y * a.x);  // conj(s) a
-        col[k] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
-        col[k + 1] = make_double2(-csa.x + c * b.x, -csa.y + c * b.y);
-    }
-    // new rotation zeroing col[j+1]
-    const double2 a = col[j], b = col[j + 1];
-    const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
-    double c;
-    double2 s;
-    if (nb == 0.0) {
-        c = 1.0;
-        s = make_double2(0, 0);
-    } else if (na == 0.0) {
-        c = 0.0;
-        s = make_double2(b.x / nb, -b.y / nb);  // conj(b)/|b|
-    } else {
-        const double t = hypot(na, nb);
-        c = na / t;
-        const double2 ua = make_double2(a.x / na, a.y / na);  // a/|a|
-        // s = (a/|a|) conj(b) / t
-        s = make_double2((ua.x * b.x + ua.y * b.y) / t, (ua.y * b.x - ua.x * b.y) / t);
-    }
-    cs[j] = make_double2(c, 0.0);
-    sn[j] = s;
-    const double2 sb = cmul(s, b);
-    col[j] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
-    col[j + 1] = make_double2(0.0, 0.0);
-    const double2 gj = g[j];
-    const double2 csg = make_double2(s.x * gj.x + s.y * gj.y, s.x * gj.y - s.y * gj.x);  // conj(s) g_j
-    g[j] = make_double2(c * gj.x, c * gj.y);
-    g[j + 1] = make_double2(-csg.x, -csg.y);
-    *res = hypot(g[j + 1].x, g[j + 1].y);
-}
-
-// Back substitution H[0:n,0:n] y = g[0:n] (one thread).
-__global__ void backsolve_kernel(int n, int m, const double2* __restrict__ H, const double2* __restrict__ g, double2* __restrict__ y)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double2 yi;
+    const int t = threadIdx.x;
+    double2 gt = t < n ? g[t] : make_double2(0, 0);
     for (int i = n - 1; i >= 0; i--) {
-        double2 t = g[i];
-        for (int k = i + 1; k < n; k++) {
-            const double2 p = cmul(H[(size_t)k * (m + 1) + i], y[k]);
-            t.x -= p.x;
-            t.y -= p.y;
+        if (t == i) {
+            const double2 d = H[(size_t)i * (m + 1) + i];
+            const double dd = d.x * d.x + d.y * d.y;
+            const double2 v = dd > 0 ? make_double2((gt.x * d.x + gt.y * d.y) / dd, (gt.y * d.x - gt.x * d.y) / dd) : make_double2(0, 0);
+            y[i] = v;
+            yi = v;
         }
-        const double2 d = H[(size_t)i * (m + 1) + i];
-        const double dd = d.x * d.x + d.y * d.y;
-        y[i] = dd > 0 ? make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd) : make_double2(0, 0);
+        __syncthreads();
+        if (t < i) {
+            const double2 p = cmul(H[(size_t)i * (m + 1) + t], yi);
+            gt.x -= p.x;
+            gt.y -= p.y;
+        }
+        __syncthreads();
     }
 }
 
@@ -219,6 +351,42 @@ __global__ void init_g_kernel(int m, const double2* __restrict__ rn2, double2* _
     if (k <= m) g[k] = k == 0 ? make_double2(sqrt(rn2->x), 0.0) : make_double2(0, 0);
 }
 
+unsigned blocks(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+// Workspace of one operator handle, kept between solves (grown on demand).
+struct GmresWork {
+    long N = 0;
+    int m = 0, nrb = 0;
+    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t = nullptr, *zin = nullptr;
+    double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double2 *h1 = nullptr, *h2 = nullptr, *part = nullptr, *sc = nullptr;  // sc: scalars (norms^2)
+    double* res = nullptr;       // device: |g[j+1]| per step
+    double* res_host = nullptr;  // pinned: one slot per step
+    unsigned* tickets = nullptr;
+    cudaEvent_t ev[2] = {};
+    void release()
+    {
+        for (void* p : {(void*)V, (void*)Z, (void*)w, (void*)r, (void*)t, (void*)zin, (void*)H, (void*)cs, (void*)sn, (void*)g, (void*)y, (void*)h1,
+                        (void*)h2, (void*)part, (void*)sc, (void*)res, (void*)tickets})
+            cudaFree(p);
+        if (res_host) cudaFreeHost(res_host);
+        for (cudaEvent_t& e : ev)
+            if (e) cudaEventDestroy(e);
+        *this = GmresWork();
+    }
+};
+
+void gmres_work_free(GmresWork* w)
+{
+    if (!w) return;
+    w->release();
+    delete w;
+}
+
+namespace {
+
 template <typename P>
 void dalloc(P** p, size_t bytes)
 {
@@ -228,44 +396,15 @@ void dalloc(P** p, size_t bytes)
     }
 }
 
-struct Work {
-    long N = 0;
-    int m = 0, nrb = 0;
-    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t = nullptr, *zin = nullptr;
-    double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
-    double2 *h1 = nullptr, *h2 = nullptr, *part = nullptr, *sc = nullptr;  // sc: scalars (norms^2)
-    double* res = nullptr;
-    double* res_host = nullptr;  // pinned
-    ~Work()
-    {
-        for (void* p : {(void*)V, (void*)Z, (void*)w, (void*)r, (void*)t, (void*)zin, (void*)H, (void*)cs, (void*)sn, (void*)g, (void*)y, (void*)h1,
-                        (void*)h2, (void*)part, (void*)sc, (void*)res})
-            cudaFree(p);
-        if (res_host) cudaFreeHost(res_host);
-    }
-};
-
-unsigned blocks(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
-
-// out[0..nk) = V[:, 0..nk)^H w  (accumulate: out += ...)
-void dots(Work& W, const double2* V, long ldv, int nk, const double2* w, double2* out, int accumulate, cudaStream_t s)
+GmresWork& workspace(OpsDev& d, long N, int m)
 {
-    dots_partial_kernel<<<dim3(W.nrb, nk), kThreads, 0, s>>>(W.N, V, ldv, nk, w, W.part, W.nrb);
-    dots_final_kernel<<<(nk + 127) / 128, 128, 0, s>>>(nk, W.nrb, W.part, out, accumulate);
-}
-
-}  // namespace
-
-int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double* f, double* x, const gmres_opts& o, gmres_stats& st,
-              cudaStream_t s)
-{
-    auto t0 = std::chrono::steady_clock::now();
-    const long N = t.N;
-    const int m = o.restart;
-    Work W;
+    if (!d.gw) d.gw = new GmresWork();
+    GmresWork& W = *d.gw;
+    if (W.N == N && W.m >= m) return W;
+    W.release();
     W.N = N;
     W.m = m;
-    W.nrb = (int)((N + kRowBlock - 1) / kRowBlock);
+    W.nrb = (int)((N + kCR - 1) / kCR);
     dalloc(&W.V, sizeof(double2) * N * (m + 1));
     dalloc(&W.Z, sizeof(double2) * N * m);
     dalloc(&W.w, sizeof(double2) * N);
@@ -282,20 +421,45 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
     dalloc(&W.part, sizeof(double2) * (size_t)W.nrb * (m + 1));
     dalloc(&W.sc, sizeof(double2) * 4);
     dalloc(&W.res, sizeof(double));
-    if (cudaMallocHost(&W.res_host, sizeof(double)) != cudaSuccess) {
+    dalloc(&W.tickets, sizeof(unsigned) * 4);
+    CK(cudaMemset(W.tickets, 0, sizeof(unsigned) * 4));
+    if (cudaMallocHost(&W.res_host, sizeof(double) * (m + 1)) != cudaSuccess) {
         cudaGetLastError();
         fail(DAFMM_ENOMEM, "pinned host allocation for GMRES failed");
     }
+    for (cudaEvent_t& e : W.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    const int tile_max = (int)(sizeof(double2) * kCR * (kMaxM + 1));
+    CK(cudaFuncSetAttribute(cgs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max));
+    CK(cudaFuncSetAttribute(cgs_norm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max));
+    return W;
+}
+
+// |v|^2 -> *out (real part), no Givens step.
+void norm2(GmresWork& W, const double2* v, double2* out, cudaStream_t s)
+{
+    GivensArgs none{};
+    cgs_norm_kernel<<<W.nrb, kAT, 0, s>>>(W.N, nullptr, 0, nullptr, (double2*)v, W.part, W.tickets + 3, out, none);
+}
+
+}  // namespace
+
+int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double* f, double* x, const gmres_opts& o, gmres_stats& st,
+              cudaStream_t s)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const long N = t.N;
+    const int m = o.restart;
+    if (m < 1 || m > kMaxM) fail(DAFMM_EBADARG, "restart must be in 1..128");
+    GmresWork& W = workspace(d, N, m);
     double2* X = (double2*)x;
     const double2* F = (const double2*)f;
-    auto norm2 = [&](const double2* v, double2* out) { dots(W, v, N, 1, v, out, 0, s); };
     auto read_sqrt = [&](const double2* dev) {
         double2 h;
         CK(cudaMemcpyAsync(&h, dev, sizeof(double2), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         return std::sqrt(std::max(h.x, 0.0));
     };
-    norm2(F, W.sc);
+    norm2(W, F, W.sc, s);
     const double nf = read_sqrt(W.sc);
     std::memset(&st, 0, sizeof(st));
     if (nf == 0.0) {
@@ -304,14 +468,46 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
         st.converged = 1;
         return DAFMM_OK;
     }
+    // one Arnoldi step: column j of V -> z_j, w = A z_j, orthogonalise, Givens
+    auto enqueue_step = [&](int j) {
+        double2* vj = W.V + (size_t)j * N;
+        double2* zj = W.Z + (size_t)j * N;
+        if (prec) {
+            prec(M, (const double*)vj, (double*)zj, o.precision, s);
+            st.precond_applies++;
+        } else {
+            CK(cudaMemcpyAsync(zj, vj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        }
+        // fixed buffers keep the captured application valid from one step to the next
+        CK(cudaMemcpyAsync(W.zin, zj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        apply_matvec(t, d, 1, (const double*)W.zin, (double*)W.w, o.precision, s);
+        st.matvecs++;
+        // classical Gram-Schmidt, twice; then |w|, the Givens step and v_{j+1}
+        const size_t tile = sizeof(double2) * kCR * (size_t)(j + 1);
+        cgs_kernel<<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, nullptr, W.w, W.part, W.tickets + 0, W.h1);
+        cgs_kernel<<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, W.h1, W.w, W.part, W.tickets + 1, W.h2);
+        GivensArgs gv{j, m, W.h1, W.h2, W.H, W.cs, W.sn, W.g, W.res};
+        cgs_norm_kernel<<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, W.h2, W.w, W.part, W.tickets + 2, W.sc + 2, gv);
+        scale_inv_norm_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.w, W.sc + 2, W.V + (size_t)(j + 1) * N);
+        CK(cudaMemcpyAsync(W.res_host + j, W.res, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(W.ev[j & 1], s));
+    };
     int total = 0;
     double rel = 0;
+    // a zero initial guess needs no application for its residual
+    norm2(W, X, W.sc + 3, s);
+    bool x_zero = read_sqrt(W.sc + 3) == 0.0;
     for (int outer = 0;; outer++) {
         // true residual in FP64: r = f - A x
-        apply_matvec(t, d, 1, (const double*)X, (double*)W.t, DAFMM_FP64, s);
-        st.matvecs++;
-        sub_kernel<<<blocks(N), kThreads, 0, s>>>(N, F, W.t, W.r);
-        norm2(W.r, W.sc + 1);
+        if (x_zero) {
+            CK(cudaMemcpyAsync(W.r, F, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+            x_zero = false;
+        } else {
+            apply_matvec(t, d, 1, (const double*)X, (double*)W.t, DAFMM_FP64, s);
+            st.matvecs++;
+            sub_kernel<<<blocks(N), kThreads, 0, s>>>(N, F, W.t, W.r);
+        }
+        norm2(W, W.r, W.sc + 1, s);
         const double rn = read_sqrt(W.sc + 1);
         rel = rn / nf;
         if (o.history && total < o.history_len) o.history[total] = rel;
@@ -325,42 +521,41 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
         const double inner = o.precision == DAFMM_MIXED ? std::max(o.inner_tol, o.tol / rel * 0.5) : o.tol / rel * 0.5;
         scale_inv_norm_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.r, W.sc + 1, W.V);
         init_g_kernel<<<(m + 1 + 127) / 128, 128, 0, s>>>(m, W.sc + 1, W.g);
-        int j = 0;
-        for (; j < m && total < o.max_iters; j++) {
-            double2* vj = W.V + (size_t)j * N;
-            double2* zj = W.Z + (size_t)j * N;
-            if (prec) {
-                prec(M, (const double*)vj, (double*)zj, o.precision, s);
-                st.precond_applies++;
-            } else {
-                CK(cudaMemcpyAsync(zj, vj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        const int steps = std::min(m, o.max_iters - total);  // steps this cycle may take
+        enqueue_step(0);
+        int queued = 1, j = 0;
+        double e1 = 1.0, e2 = 1.0;  // the last two estimates (relative to |r|)
+        for (;; j++) {
+            // queue step j + 1 now if the estimates predict that step j misses the
+            // target by far (a needless step costs a full application; waiting
+            // costs only the time to queue the next launch)
+            if (queued == j + 1 && j + 1 < steps) {
+                const double pred = j >= 2 ? e1 * std::min(1.0, e1 / e2) : e1;
+                if (pred > 30.0 * inner) {
+                    enqueue_step(j + 1);
+                    queued++;
+                }
             }
-            // fixed buffers keep the captured application valid from one iteration to the next
-            CK(cudaMemcpyAsync(W.zin, zj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
-            apply_matvec(t, d, 1, (const double*)W.zin, (double*)W.w, o.precision, s);
-            st.matvecs++;
-            // classical Gram-Schmidt, twice
-            dots(W, W.V, N, j + 1, W.w, W.h1, 0, s);
-            sub_vh_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.V, N, j + 1, W.h1, W.w);
-            dots(W, W.V, N, j + 1, W.w, W.h2, 0, s);
-            sub_vh_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.V, N, j + 1, W.h2, W.w);
-            norm2(W.w, W.sc + 2);
-            scale_inv_norm_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.w, W.sc + 2, W.V + (size_t)(j + 1) * N);
-            givens_kernel<<<1, 1, 0, s>>>(j, m, W.h1, W.h2, W.sc + 2, W.H, W.cs, W.sn, W.g, W.res);
-            CK(cudaMemcpyAsync(W.res_host, W.res, sizeof(double), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
+            CK(cudaEventSynchronize(W.ev[j & 1]));
             total++;
-            const double est = *W.res_host / rn;  // relative to this cycle's |r|
+            const double est = W.res_host[j] / rn;
             if (o.history && total < o.history_len) o.history[total] = est * rel;
-            if (est <= inner) {
+            if (est <= inner || j + 1 >= steps) {
                 j++;
                 break;
             }
+            if (queued == j + 1) {
+                enqueue_step(j + 1);
+                queued++;
+            }
+            e2 = e1;
+            e1 = est;
         }
-        backsolve_kernel<<<1, 1, 0, s>>>(j, m, W.H, W.g, W.y);
+        backsolve_kernel<<<1, kMaxM, 0, s>>>(j, m, W.H, W.g, W.y);
         add_zy_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.Z, N, j, W.y, X);
         CK(cudaGetLastError());
     }
+    CK(cudaStreamSynchronize(s));
     st.iterations = total;
     st.rel_residual = rel;
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

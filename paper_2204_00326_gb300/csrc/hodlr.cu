@@ -86,6 +86,8 @@ struct HodlrLevelHost {
     std::vector<cd> U;     // N x r: the uncorrected U12 / U21 (kept for the dense export)
 };
 
+constexpr int kHodlrMaxLevels = 24;  // levels of the apply launch
+
 struct HodlrDevLevel {
     int r = 0;
     double2 *R64 = nullptr, *Ut64 = nullptr, *S64 = nullptr;
@@ -105,9 +107,18 @@ struct dafmm_hodlr {
     double2* inv64 = nullptr;
     float2* inv32 = nullptr;
     std::vector<dafmm::HodlrDevLevel> dlv;
-    void* t_part = nullptr;  // reduction partials (complex128 size): rmax x N/32
-    void* s_buf = nullptr;   // s per node and half: 2 rmax x nodes
+    void* t_part = nullptr;  // partial sums of W x (complex128 size): rmax x N / leaf
+    void* s_buf = nullptr;   // s per node, two parity halves of 2 rmax x N / leaf
     void* xw = nullptr;      // complex64 work vector (mixed precision)
+    long sbuf_half = 0;      // entries of one parity half of s_buf
+    int* cnt = nullptr;      // per-node arrival counters of the apply launch
+    long ncnt = 0;
+    unsigned* bar = nullptr;  // grid barrier: arrivals, exits
+    int* err = nullptr;       // set when a wait of the apply gave up
+    int ncta = 1;             // CTAs of the apply launch
+    int ncta_default = 1;     // the width chosen at build
+    long ncta_cap = 1;        // CTAs resident at once
+    mutable int stall = 0;    // test support: the next apply waits for one CTA too many
     int rmax = 0;
     double seconds = 0;
 };
@@ -217,140 +228,428 @@ __device__ __forceinline__ C cmul(C a, C b)
     return r;
 }
 
-// x_leaf = Inv_leaf b_leaf; one CTA (leaf threads) per leaf; Inv column-major.
+// ------------------------------------------------------------------------
+// The application x = A~^{-1} b is one cooperative launch.  CTA c owns the
+// unknowns [c E, (c + 1) E) (E a power of two, a multiple of the leaf size):
+//   1. x = D^{-1} b on its leaves;
+//   then for every level l from the leaves up (n = N >> l, halves of h = n/2):
+//   2. partial sums of t = W x over its segments (min(E, h) unknowns each);
+//   3. the last CTA to finish a node (an arrival counter per node) sums the
+//      partials into t and forms s = S^{-1} t for that node;
+//   4. grid barrier (every node's s is written);
+//   5. x -= Ut s on its unknowns.
+// Steps 5 and 2 of the next level touch only the CTA's own unknowns, so one
+// barrier per level suffices.  Every wait has a time limit, after which the
+// launch sets the handle's error flag and returns.
+
+constexpr int kHT = 256;                              // threads per CTA
+constexpr unsigned long long kHWaitNs = 200000000ull;  // 0.2 s per barrier
+
 template <typename T>
-__global__ void leaf_inv_kernel(int leaf, const typename C2<T>::t* __restrict__ inv, const typename C2<T>::t* __restrict__ b,
-                                typename C2<T>::t* __restrict__ x)
-{
+struct HArgs {
     using C = typename C2<T>::t;
-    extern __shared__ unsigned char sm_raw[];
-    C* bs = (C*)sm_raw;
-    const long base = (long)blockIdx.x * leaf;
-    for (int j = threadIdx.x; j < leaf; j += blockDim.x) bs[j] = b[base + j];
+    long N;
+    int H, lf, ncta, extra;
+    long E;
+    const C* inv;        // leaf inverses, column-major lf x lf per leaf
+    const double2* b;    // right-hand side (complex128)
+    double2* xout;       // result (complex128)
+    C* x;                // work vector (xout itself in complex128)
+    C* part;             // partial sums, [q][segment]
+    C* sbuf;             // s per node, two buffers by level parity: [parity][node][2 r]
+    long sbuf_half;      // entries per parity buffer
+    int* cnt;            // arrival counters per node (zero between launches)
+    unsigned* bar;       // [0] barrier arrivals, [1] exits
+    int* err;
+    const C* R[kHodlrMaxLevels];  // r x N
+    const C* U[kHodlrMaxLevels];  // Ut transposed: r x N
+    const C* S[kHodlrMaxLevels];  // per node 2r x 2r row-major
+    int r[kHodlrMaxLevels];
+};
+
+__device__ __forceinline__ unsigned long long h_clock()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned h_ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier: arrive, then wait until target arrivals (with a time and an
+// iteration limit).  False, with *err set, when the wait gave up.
+__device__ bool h_barrier(unsigned* arrive, unsigned target, int* err)
+{
+    __threadfence();
     __syncthreads();
-    const C* M = inv + (size_t)blockIdx.x * leaf * leaf;
-    for (int i = threadIdx.x; i < leaf; i += blockDim.x) {
-        T sr = 0, si = 0;
-        for (int j = 0; j < leaf; j++) {
-            const C m = M[(size_t)j * leaf + i];
-            const C v = bs[j];
-            sr += m.x * v.x - m.y * v.y;
-            si += m.x * v.y + m.y * v.x;
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        atomicAdd(arrive, 1u);
+        const unsigned long long t0 = h_clock();
+        for (unsigned it = 0; h_ld_acquire(arrive) < target; it++) {
+            if (it > (1u << 24) || h_clock() - t0 > kHWaitNs) {
+                atomicExch(err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
         }
-        C o;
-        o.x = sr;
-        o.y = si;
-        x[base + i] = o;
+        __threadfence();
     }
+    return __syncthreads_and(ok) != 0;
 }
 
-// part[q][g] = sum_{i in group g of 32} R[q][i] x[i]  (segments are >= 32 long)
-template <typename T>
-__global__ void rx_partial_kernel(long N, int r, const typename C2<T>::t* __restrict__ R, const typename C2<T>::t* __restrict__ x,
-                                  typename C2<T>::t* __restrict__ part)
+// Bring [p, p + bytes) into L2 (16-byte aligned, a multiple of 16 bytes).
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes)
 {
-    using C = typename C2<T>::t;
-    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const int q = blockIdx.y;
-    C p;
-    p.x = 0;
-    p.y = 0;
-    if (i < N) p = cmul(R[(size_t)q * N + i], x[i]);
-    for (int o = 16; o > 0; o >>= 1) {
-        p.x += __shfl_down_sync(0xffffffffu, p.x, o);
-        p.y += __shfl_down_sync(0xffffffffu, p.y, o);
-    }
-    if ((threadIdx.x & 31) == 0 && i < N) part[(size_t)q * (N / 32) + i / 32] = p;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// One CTA per node: t = [V12 x2; V21 x1] from the partials, s = S^{-1} t.
-template <typename T>
-__global__ void node_small_kernel(long N, long n, int r, const typename C2<T>::t* __restrict__ part,
-                                  const typename C2<T>::t* __restrict__ S, typename C2<T>::t* __restrict__ s)
+template <typename C>
+__device__ __forceinline__ void cmac(float& sr, float& si, C m, C v)
 {
-    using C = typename C2<T>::t;
-    extern __shared__ unsigned char sm_raw[];
-    C* t = (C*)sm_raw;
-    const long node = blockIdx.x;
-    const long g0 = node * n / 32, gh = n / 64;  // groups of the node, of one half
-    for (int a = threadIdx.x; a < 2 * r; a += blockDim.x) {
-        const int q = a < r ? a : a - r;
-        const long gs = a < r ? g0 + gh : g0;  // first r: half 2 (V12 x2); last r: half 1 (V21 x1)
-        T sr = 0, si = 0;
-        for (long g = 0; g < gh; g++) {
-            const C p = part[(size_t)q * (N / 32) + gs + g];
-            sr += p.x;
-            si += p.y;
+    sr = fmaf(m.x, v.x, fmaf(-m.y, v.y, sr));
+    si = fmaf(m.x, v.y, fmaf(m.y, v.x, si));
+}
+template <typename C>
+__device__ __forceinline__ void cmac(double& sr, double& si, C m, C v)
+{
+    sr = fma(m.x, v.x, fma(-m.y, v.y, sr));
+    si = fma(m.x, v.y, fma(m.y, v.x, si));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Lane sums of four (re, im) accumulators, interleaved.
+template <typename T>
+__device__ __forceinline__ void warp_sum4(T (&re)[4], T (&im)[4])
+{
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            re[u] += __shfl_xor_sync(0xffffffffu, re[u], o);
+            im[u] += __shfl_xor_sync(0xffffffffu, im[u], o);
         }
-        t[a].x = sr;
-        t[a].y = si;
+}
+
+// This CTA's columns [e0, e0 + E) of R and Ut of level l to L2.
+template <typename T>
+__device__ __forceinline__ void prefetch_rows(const HArgs<T>& a, int l, long e0, int tid)
+{
+    using C = typename C2<T>::t;
+    if (l < 0) return;
+    const int r = a.r[l];
+    for (int k = tid; k < 2 * r; k += kHT) {
+        const C* base = k < r ? a.R[l] + (size_t)k * a.N : a.U[l] + (size_t)(k - r) * a.N;
+        for (long o = 0; o < a.E; o += 2048) l2_prefetch(base + e0 + o, (unsigned)(min(a.E - o, 2048L) * sizeof(C)));
     }
-    __syncthreads();
-    const C* Sn = S + (size_t)node * 4 * r * r;
-    for (int a = threadIdx.x; a < 2 * r; a += blockDim.x) {
-        T sr = 0, si = 0;
-        for (int b = 0; b < 2 * r; b++) {
-            const C m = Sn[(size_t)a * 2 * r + b];
-            sr += m.x * t[b].x - m.y * t[b].y;
-            si += m.x * t[b].y + m.y * t[b].x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant__ HArgs<T> a)
+{
+    using C = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char hsm[];
+    C* sh = (C*)hsm;
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kW = kHT / 32;
+    const long E = a.E, e0 = (long)blockIdx.x * E;
+    const int lf = a.lf;
+    // factors to L2 ahead of use: a 1/ncta slice of every level's S blocks
+    // now, this CTA's columns of R and Ut one level ahead (prefetch_rows)
+    prefetch_rows(a, a.H - 1, e0, tid);
+    for (int l = a.H - 1; l >= 0; l--) {
+        const int r = a.r[l];
+        if (tid == 0 && r > 0) {
+            const size_t sb = (size_t)(1L << l) * 4 * r * r * sizeof(C);
+            const size_t sl = (sb / a.ncta + 15) / 16 * 16, b0 = (size_t)blockIdx.x * sl;
+            for (size_t o = b0; o < min(sb, b0 + sl); o += 32768)
+                l2_prefetch((const char*)a.S[l] + o, (unsigned)min((size_t)32768, min(sb, b0 + sl) - o));
         }
-        s[(size_t)node * 2 * r + a].x = sr;
-        s[(size_t)node * 2 * r + a].y = si;
     }
-}
-
-// x[i] -= sum_q Ut[i][q] s[node(i)][half(i)][q]
-template <typename T>
-__global__ void update_kernel(long N, long n, int r, const typename C2<T>::t* __restrict__ Ut, const typename C2<T>::t* __restrict__ s,
-                              typename C2<T>::t* __restrict__ x)
-{
-    using C = typename C2<T>::t;
-    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const long node = i / n;
-    const int hh = (i - node * n) >= n / 2 ? 1 : 0;
-    const C* sv = s + (size_t)node * 2 * r + hh * r;
-    const C* u = Ut + (size_t)i * r;
-    C a = x[i];
-    for (int q = 0; q < r; q++) {
-        const C p = cmul(u[q], sv[q]);
-        a.x -= p.x;
-        a.y -= p.y;
+    // 1. leaf inverses, `per` unknowns (whole leaves) staged at a time, so that x may alias b
+    const long per = min(E, (long)max(lf, kHT));
+    for (long g0 = e0; g0 < e0 + E; g0 += per) {
+        __syncthreads();
+        for (long k = tid; k < per; k += kHT) {
+            const double2 v = a.b[g0 + k];
+            C c;
+            c.x = (T)v.x;
+            c.y = (T)v.y;
+            sh[k] = c;
+        }
+        __syncthreads();
+        for (long k = tid; k < per; k += kHT) {
+            const long li = k / lf * lf, i = k - li;
+            const C* M = a.inv + (size_t)((g0 + li) / lf) * lf * lf + i;
+            T sr = 0, si = 0;
+            for (int j = 0; j < lf; j++) cmac(sr, si, M[(size_t)j * lf], sh[li + j]);
+            C o;
+            o.x = sr;
+            o.y = si;
+            a.x[g0 + k] = o;
+        }
     }
-    x[i] = a;
-}
-
-__global__ void c128_to_c64(long n, const double2* __restrict__ a, float2* __restrict__ b)
-{
-    long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (k < n) b[k] = make_float2((float)a[k].x, (float)a[k].y);
-}
-__global__ void c64_to_c128(long n, const float2* __restrict__ a, double2* __restrict__ b)
-{
-    long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (k < n) b[k] = make_double2(a[k].x, a[k].y);
-}
-
-template <typename T>
-void apply(const dafmm_hodlr& h, const typename C2<T>::t* b, typename C2<T>::t* x, cudaStream_t s)
-{
-    using C = typename C2<T>::t;
-    const long N = h.N;
-    const long nleaf = N / h.leaf;
-    const C* inv = (const C*)(sizeof(T) == 8 ? (const void*)h.inv64 : (const void*)h.inv32);
-    leaf_inv_kernel<T><<<(unsigned)nleaf, std::min(h.leaf, 256), sizeof(C) * h.leaf, s>>>(h.leaf, inv, b, x);
-    for (int l = h.H - 1; l >= 0; l--) {
-        const HodlrDevLevel& L = h.dlv[l];
-        const int r = L.r;
+    bool ok = true;
+    unsigned nb = 0;
+    for (int l = a.H - 1; l >= 0; l--) {
+        const int r = a.r[l];
         if (r == 0) continue;
-        const long n = N >> l;
-        const C* R = (const C*)(sizeof(T) == 8 ? (const void*)L.R64 : (const void*)L.R32);
-        const C* Ut = (const C*)(sizeof(T) == 8 ? (const void*)L.Ut64 : (const void*)L.Ut32);
-        const C* S = (const C*)(sizeof(T) == 8 ? (const void*)L.S64 : (const void*)L.S32);
-        rx_partial_kernel<T><<<dim3((unsigned)((N + 255) / 256), r), 256, 0, s>>>(N, r, R, x, (C*)h.t_part);
-        node_small_kernel<T><<<(unsigned)(N / n), 64, sizeof(C) * 2 * r, s>>>(N, n, r, (const C*)h.t_part, S, (C*)h.s_buf);
-        update_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, n, r, Ut, (const C*)h.s_buf, x);
+        const long n = a.N >> l, h = n >> 1;
+        const long m = min(E, h), nslots = a.N / m;
+        const C* R = a.R[l];
+        prefetch_rows(a, l - 1, e0, tid);
+        __syncthreads();  // this CTA's x is final for the level
+        // 2. partials of W x: part[q][segment] over each of this CTA's segments
+        // (four rows q of R per warp at a time, so that their loads overlap)
+        for (long s0 = e0; s0 < e0 + E; s0 += m) {
+            for (int q0 = warp; q0 < r; q0 += 4 * kW) {
+                T sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
+                for (long i = s0 + lane; i < s0 + m; i += 32) {
+                    const C xv = a.x[i];
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (q0 + u * kW < r) cmac(sr[u], si[u], R[(size_t)(q0 + u * kW) * a.N + i], xv);
+                }
+                warp_sum4(sr, si);
+                if (lane < 4 && q0 + lane * kW < r) {
+                    C o;
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (u == lane) {
+                            o.x = sr[u];
+                            o.y = si[u];
+                        }
+                    a.part[(size_t)(q0 + lane * kW) * nslots + s0 / m] = o;
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        // 3. s = S^{-1} t for every node this CTA completes
+        C* sb = a.sbuf + (size_t)(l & 1) * a.sbuf_half;
+        const long nodes_here = E >= n ? E / n : 1, node0 = e0 / n;
+        for (long nd = node0; nd < node0 + nodes_here; nd++) {
+            if (E < n) {
+                if (tid == 0) {
+                    const int last = atomicAdd(&a.cnt[nd], 1) == (int)(n / E) - 1;
+                    if (last) a.cnt[nd] = 0;
+                    __threadfence();
+                    s_last = last;
+                }
+                __syncthreads();
+                if (!s_last) continue;
+            }
+            // t[0..r): half 2 (V12 x2); t[r..2r): half 1 (V21 x1).  Rows are
+            // split over p consecutive lanes (p a power of two, 2r p <= kHT
+            // where possible) so that every thread's loads go out together.
+            const int R2 = 2 * r;
+            int p = 1;
+            while (p < 32 && 2 * p * R2 <= kHT) p *= 2;
+            const int rpp = kHT / p, npass = (R2 + rpp - 1) / rpp, piece = tid % p;
+            const long gh = h / m, g1 = nd * n / m;
+            for (int pass = 0; pass < npass; pass++) {
+                const int aa = pass * rpp + tid / p;
+                T sr = 0, si = 0;
+                if (aa < R2) {
+                    const int q = aa < r ? aa : aa - r;
+                    const C* P = a.part + (size_t)q * nslots + (aa < r ? g1 + gh : g1);
+#pragma unroll 8
+                    for (long k = piece; k < gh; k += p) {
+                        const C v = __ldcg(P + k);
+                        sr += v.x;
+                        si += v.y;
+                    }
+                }
+                for (int o = p / 2; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (aa < R2 && piece == 0) {
+                    C o;
+                    o.x = sr;
+                    o.y = si;
+                    sh[aa] = o;
+                }
+            }
+            __syncthreads();
+            const C* Sn = a.S[l] + (size_t)nd * 4 * r * r;
+            const int cols = (R2 + p - 1) / p;
+            for (int pass = 0; pass < npass; pass++) {
+                const int aa = pass * rpp + tid / p;
+                T sr = 0, si = 0;
+                if (aa < R2) {
+                    const C* row = Sn + (size_t)aa * R2;
+                    const int b1 = min(R2, (piece + 1) * cols);
+#pragma unroll 8
+                    for (int bb = piece * cols; bb < b1; bb++) cmac(sr, si, row[bb], sh[bb]);
+                }
+                for (int o = p / 2; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (aa < R2 && piece == 0) {
+                    C o;
+                    o.x = sr;
+                    o.y = si;
+                    sb[(size_t)nd * 2 * r + aa] = o;
+                }
+            }
+            __syncthreads();
+        }
+        // 4. every node's s is written
+        nb++;
+        if (!h_barrier(&a.bar[0], nb * (unsigned)a.ncta + (unsigned)a.extra, a.err)) {
+            ok = false;
+            break;
+        }
+        // 5. x -= Ut s on this CTA's unknowns, one segment (one half's s, staged
+        // in shared memory) at a time; a segment shorter than the CTA splits
+        // the sum over q between tpe threads per unknown
+        const C* U = a.U[l];
+        const int tpe = m >= kHT ? 1 : (int)(kHT / m);
+        C* red = sh + 2 * r;  // tpe x m partial sums (tpe > 1)
+        for (long s0 = e0; s0 < e0 + E; s0 += m) {
+            const long nd = s0 / n;
+            const C* sv = sb + (size_t)nd * 2 * r + ((s0 - nd * n) >= h ? r : 0);
+            __syncthreads();
+            for (int q = tid; q < r; q += kHT) sh[q] = __ldcg(sv + q);
+            __syncthreads();
+            const int g = tid / (int)min(m, (long)kHT);
+            for (long k = tid % min(m, (long)kHT); k < m; k += min(m, (long)kHT)) {
+                const long i = s0 + k;
+                T sr = 0, si = 0;
+                int q = g;
+                for (; q + 7 * tpe < r; q += 8 * tpe) {
+                    C u[8];
+#pragma unroll
+                    for (int v = 0; v < 8; v++) u[v] = U[(size_t)(q + v * tpe) * a.N + i];
+#pragma unroll
+                    for (int v = 0; v < 8; v++) cmac(sr, si, u[v], sh[q + v * tpe]);
+                }
+                for (; q < r; q += tpe) cmac(sr, si, U[(size_t)q * a.N + i], sh[q]);
+                if (tpe == 1) {
+                    C x = a.x[i];
+                    x.x -= sr;
+                    x.y -= si;
+                    a.x[i] = x;
+                } else {
+                    C o;
+                    o.x = sr;
+                    o.y = si;
+                    red[(size_t)g * m + k] = o;
+                }
+            }
+            if (tpe > 1) {
+                __syncthreads();
+                for (long k = tid; k < m; k += kHT) {
+                    C x = a.x[s0 + k];
+                    for (int gg = 0; gg < tpe; gg++) {
+                        x.x -= red[(size_t)gg * m + k].x;
+                        x.y -= red[(size_t)gg * m + k].y;
+                    }
+                    a.x[s0 + k] = x;
+                }
+            }
+        }
     }
+    if (ok && sizeof(T) == 4)
+        for (long i = e0 + tid; i < e0 + E; i += kHT) a.xout[i] = make_double2(a.x[i].x, a.x[i].y);
+    // the last CTA to leave re-arms the barrier for the next launch
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&a.bar[1], 1u) == (unsigned)a.ncta - 1) {
+            a.bar[0] = 0;
+            a.bar[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <typename T>
+size_t apply_smem(const dafmm_hodlr& h)
+{
+    using C = typename C2<T>::t;
+    return sizeof(C) * (size_t)std::max<long>(std::max(h.leaf, kHT), 2L * std::max(h.rmax, 1) + kHT);
+}
+
+template <typename T>
+void apply(const dafmm_hodlr& h, const double2* b, double2* xout, cudaStream_t s)
+{
+    using C = typename C2<T>::t;
+    HArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = h.N;
+    a.H = h.H;
+    a.lf = h.leaf;
+    a.ncta = h.ncta;
+    a.E = h.N / h.ncta;
+    a.extra = h.stall ? 1 : 0;
+    h.stall = 0;
+    a.inv = (const C*)(sizeof(T) == 8 ? (const void*)h.inv64 : (const void*)h.inv32);
+    a.b = b;
+    a.xout = xout;
+    a.x = sizeof(T) == 8 ? (C*)xout : (C*)h.xw;
+    a.part = (C*)h.t_part;
+    a.sbuf = (C*)h.s_buf;
+    a.sbuf_half = h.sbuf_half;
+    a.cnt = h.cnt;
+    a.bar = h.bar;
+    a.err = h.err;
+    for (int l = 0; l < h.H; l++) {
+        const HodlrDevLevel& L = h.dlv[l];
+        a.r[l] = L.r;
+        a.R[l] = (const C*)(sizeof(T) == 8 ? (const void*)L.R64 : (const void*)L.R32);
+        a.U[l] = (const C*)(sizeof(T) == 8 ? (const void*)L.Ut64 : (const void*)L.Ut32);
+        a.S[l] = (const C*)(sizeof(T) == 8 ? (const void*)L.S64 : (const void*)L.S32);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)h.ncta);
+    cfg.blockDim = dim3(kHT);
+    cfg.dynamicSmemBytes = apply_smem<T>(h);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, hodlr_apply_kernel<T>, a));
+}
+
+// Co-resident CTA capacity of the launch (both precisions).
+long apply_capacity(const dafmm_hodlr& h)
+{
+    int dev = 0, sms = 0, p32 = 0, p64 = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t s32 = apply_smem<float>(h), s64 = apply_smem<double>(h);
+    CK(cudaFuncSetAttribute(hodlr_apply_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
+    CK(cudaFuncSetAttribute(hodlr_apply_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, hodlr_apply_kernel<float>, kHT, s32));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, hodlr_apply_kernel<double>, kHT, s64));
+    return (long)sms * std::max(0, std::min(p32, p64));
+}
+
+// Default width: a power of two, resident at once, at most one CTA per leaf,
+// about 2048 unknowns per CTA on large problems (at least 128 CTAs).
+int apply_ctas(const dafmm_hodlr& h)
+{
+    const long want = std::min({h.ncta_cap, h.N / h.leaf, std::max(128L, h.N / 2048)});
+    long c = 1;
+    while (2 * c <= want) c *= 2;
+    return (int)c;
 }
 
 }  // namespace
@@ -360,17 +659,38 @@ const dafmm_tree* hodlr_tree(const dafmm_hodlr* h) { return h->tree; }
 void hodlr_apply(const dafmm_hodlr* h, const double* b, double* x, int precision, cudaStream_t s)
 {
     cudaGetLastError();
-    const long N = h->N;
-    if (precision == DAFMM_FP64) {
+    if (precision == DAFMM_FP64)
         apply<double>(*h, (const double2*)b, (double2*)x, s);
-    } else {
-        float2* w = (float2*)h->xw;
-        float2* w2 = w + N;
-        c128_to_c64<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, (const double2*)b, w2);
-        apply<float>(*h, w2, w, s);
-        c64_to_c128<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, w, (double2*)x);
-    }
+    else
+        apply<float>(*h, (const double2*)b, (double2*)x, s);
     CK(cudaGetLastError());
+}
+
+int hodlr_check(const dafmm_hodlr* h, cudaStream_t s)
+{
+    CK(cudaStreamSynchronize(s));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return DAFMM_OK;
+    // a launch that gave up may have left node counters armed
+    CK(cudaMemset(h->cnt, 0, sizeof(int) * (size_t)h->ncnt));
+    CK(cudaMemset(h->bar, 0, 2 * sizeof(unsigned)));
+    CK(cudaMemset(h->err, 0, sizeof(int)));
+    return DAFMM_ETIMEOUT;
+}
+
+void hodlr_set_stall(const dafmm_hodlr* h, int on) { h->stall = on ? 1 : 0; }
+
+void hodlr_set_width(dafmm_hodlr* h, int ctas)
+{
+    if (ctas == 0) {
+        h->ncta = h->ncta_default;
+        return;
+    }
+    if (ctas < 0 || (ctas & (ctas - 1)) || ctas > h->N / h->leaf || ctas > h->ncta_cap)
+        fail(DAFMM_EBADARG, "CTAs must be a power of two, at most one per leaf (" + std::to_string(h->N / h->leaf) +
+                                ") and at most the resident capacity (" + std::to_string(h->ncta_cap) + ")");
+    h->ncta = ctas;
 }
 
 void hodlr_prec(const void* M, const double* v, double* z, int precision, cudaStream_t s)
@@ -393,6 +713,7 @@ dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf)
         h->leaf = (int)std::min<long>(leaf, N);
         int H = 0;
         while ((N >> H) > h->leaf) H++;
+        if (H > kHodlrMaxLevels) fail(DAFMM_EBADARG, "too many HODLR levels; use a larger leaf size");
         h->H = H;
         // contrast on the host: A_ij = delta_ij + kappa^2 q_i K_ij
         std::vector<double> q(N);
@@ -499,18 +820,31 @@ dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf)
             h->rmax = std::max(h->rmax, L.r);
             up(to64(L.R), &D.R64);
             up(to32(L.R), &D.R32);
-            up(to64(L.Ut), &D.Ut64);
-            up(to32(L.Ut), &D.Ut32);
+            // Ut as r x N, so that the update reads it along the unknowns
+            std::vector<cd> utt((size_t)L.r * N);
+            for (long i = 0; i < N; i++)
+                for (int q = 0; q < L.r; q++) utt[(size_t)q * N + i] = L.Ut[(size_t)i * L.r + q];
+            up(to64(utt), &D.Ut64);
+            up(to32(utt), &D.Ut32);
             up(to64(L.Sinv), &D.S64);
             up(to32(L.Sinv), &D.S32);
         }
-        const size_t np = (size_t)std::max(1, h->rmax) * std::max<long>(N / 32, 1);
-        if (cudaMalloc(&h->t_part, sizeof(double2) * np) != cudaSuccess ||
-            cudaMalloc(&h->s_buf, sizeof(double2) * 2 * std::max(1, h->rmax) * std::max<long>(N / h->leaf, 1)) != cudaSuccess ||
-            cudaMalloc(&h->xw, sizeof(float2) * 2 * N) != cudaSuccess) {
+        const long nl = std::max<long>(N / h->leaf, 1);
+        h->sbuf_half = 2L * std::max(1, h->rmax) * nl;
+        h->ncnt = nl;
+        if (cudaMalloc(&h->t_part, sizeof(double2) * std::max(1, h->rmax) * nl) != cudaSuccess ||
+            cudaMalloc(&h->s_buf, sizeof(double2) * 2 * h->sbuf_half) != cudaSuccess ||
+            cudaMalloc(&h->xw, sizeof(float2) * N) != cudaSuccess || cudaMalloc(&h->cnt, sizeof(int) * nl) != cudaSuccess ||
+            cudaMalloc(&h->bar, 2 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&h->err, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             fail(DAFMM_ENOMEM, "device allocation for the HODLR work buffers failed");
         }
+        CK(cudaMemset(h->cnt, 0, sizeof(int) * nl));
+        CK(cudaMemset(h->bar, 0, 2 * sizeof(unsigned)));
+        CK(cudaMemset(h->err, 0, sizeof(int)));
+        h->ncta_cap = apply_capacity(*h);
+        if (h->ncta_cap < 1) fail(DAFMM_EBADARG, "the HODLR apply kernel does not fit an SM (rank too large)");
+        h->ncta = h->ncta_default = apply_ctas(*h);
     } catch (...) {
         hodlr_free(h);
         throw;
@@ -535,6 +869,9 @@ void hodlr_free(dafmm_hodlr* h)
     cudaFree(h->t_part);
     cudaFree(h->s_buf);
     cudaFree(h->xw);
+    cudaFree(h->cnt);
+    cudaFree(h->bar);
+    cudaFree(h->err);
     delete h;
 }
 

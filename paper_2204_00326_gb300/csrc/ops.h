@@ -96,6 +96,9 @@ struct GraphCache {
 };
 constexpr int kGraphSlots = 4;        // cached (v, out) pairs per precision
 
+struct GmresWork;  // GMRES workspace kept between solves (gmres.cu)
+void gmres_work_free(GmresWork* w);
+
 struct OpsDev {
     std::vector<LevelDev> lv;
     std::vector<Group> up;      // per level (index = level)
@@ -124,6 +127,7 @@ struct OpsDev {
     cudaEvent_t placeholder[5] = {};     // events recorded by freshly captured graphs
     GraphCache gc[2][kGraphSlots];
     unsigned long long gc_clock = 0;
+    GmresWork* gw = nullptr;
 };
 
 // Allocate and upload; frees host block storage as it goes.
@@ -147,6 +151,10 @@ dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf);
 void hodlr_free(dafmm_hodlr* h);
 void hodlr_apply(const dafmm_hodlr* h, const double* b, double* x, int precision, cudaStream_t s);
 void hodlr_prec(const void* M, const double* v, double* z, int precision, cudaStream_t s);
+// Synchronise s; DAFMM_ETIMEOUT (flag cleared, counters re-armed) when an apply gave up a wait.
+int hodlr_check(const dafmm_hodlr* h, cudaStream_t s);
+void hodlr_set_stall(const dafmm_hodlr* h, int on);
+void hodlr_set_width(dafmm_hodlr* h, int ctas);
 const dafmm_tree* hodlr_tree(const dafmm_hodlr* h);
 void hodlr_dense(const dafmm_hodlr* h, cd* out);
 void hodlr_shape(const dafmm_hodlr* h, long* N, int* levels, int* leaf, int* rank_max, double* seconds);

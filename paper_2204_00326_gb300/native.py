@@ -161,6 +161,9 @@ _sig = {
     "gmres_solve": ([_P, _P, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
     "hodlr_factor": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hodlr_solve": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "hodlr_sync": ([_P, _P], ctypes.c_int),
+    "hodlr_debug_stall": ([_P], ctypes.c_int),
+    "hodlr_set_ctas": ([_P, ctypes.c_int], ctypes.c_int),
     "hodlr_export": ([_P, _P], ctypes.c_int),
     "hodlr_info": ([_P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -355,6 +358,19 @@ def hodlr_factor(ops: int, rank: int = 15, tol: float = 0.0, leaf_size: int = 64
 
 def hodlr_solve(M: int, b, x, precision: int = DAFMM_FP64, stream=None) -> None:
     _check(lib.hodlr_solve(M, 1, _dptr(b, "complex128"), _dptr(x, "complex128"), precision, _stream_ptr(stream)))
+
+
+def hodlr_sync(M: int, stream=None) -> None:
+    """Synchronise; raises DafmmError (DAFMM_ETIMEOUT) if an application gave up a wait."""
+    _check(lib.hodlr_sync(M, _stream_ptr(stream)))
+
+
+def hodlr_debug_stall(M: int) -> None:
+    _check(lib.hodlr_debug_stall(M))
+
+
+def hodlr_set_ctas(M: int, ctas: int) -> None:
+    _check(lib.hodlr_set_ctas(M, int(ctas)))
 
 
 def hodlr_export(M: int, N: int) -> np.ndarray:

@@ -79,6 +79,67 @@ def test_hodlr_apply_is_inverse_of_exported_matrix(N, grid32, rank):
     N.hodlr_destroy(M)
 
 
+@pytest.mark.parametrize("leaf,ctas", [(32, 1), (32, 4), (32, 32), (64, 2), (64, 16), (256, 4), (512, 1), (512, 2)])
+def test_hodlr_apply_every_launch_width(N, grid32, leaf, ctas):
+    """One CTA may own several nodes of a level, exactly one, or part of one
+    (then the last CTA to finish the node forms s); leaves larger than the
+    CTA's thread count take several rows per thread.  Every width gives the
+    Woodbury inverse of the exported A~."""
+    w, op, A, f = grid32
+    M = N.hodlr_factor(op.ops, rank=12, leaf_size=leaf)
+    try:
+        At = N.hodlr_export(M, w.N)
+        b = W.random_vector(w.N, 1, seed=6)[:, 0]
+        ref = O.lu_solve(At, b)
+        bd = torch.as_tensor(b, device="cuda")
+        N.hodlr_set_ctas(M, ctas)
+        x = torch.empty_like(bd)
+        N.hodlr_solve(M, bd, x, N.DAFMM_FP64)
+        N.hodlr_sync(M)
+        assert _rel(x.cpu().numpy(), ref) < 1e-10
+        N.hodlr_solve(M, bd, x, N.DAFMM_MIXED)
+        N.hodlr_sync(M)
+        assert _rel(x.cpu().numpy(), ref) < 1e-4
+        N.hodlr_set_ctas(M, 0)
+    finally:
+        N.hodlr_destroy(M)
+
+
+def test_hodlr_width_argument_errors(N, grid32):
+    w, op, A, f = grid32
+    M = N.hodlr_factor(op.ops, rank=5, leaf_size=64)
+    try:
+        for bad in (3, -2, 2 * w.N // 64):
+            with pytest.raises(N.DafmmError):
+                N.hodlr_set_ctas(M, bad)
+    finally:
+        N.hodlr_destroy(M)
+
+
+def test_hodlr_barrier_timeout_is_reported_and_the_handle_recovers(N, grid32):
+    """A launch told to wait for one CTA more than it has gives up its first
+    grid barrier after about 0.2 s; hodlr_sync reports DAFMM_ETIMEOUT and the
+    next application is correct again."""
+    w, op, A, f = grid32
+    M = N.hodlr_factor(op.ops, rank=5, leaf_size=64)
+    try:
+        At = N.hodlr_export(M, w.N)
+        b = W.random_vector(w.N, 1, seed=7)[:, 0]
+        ref = O.lu_solve(At, b)
+        bd = torch.as_tensor(b, device="cuda")
+        x = torch.empty_like(bd)
+        N.hodlr_debug_stall(M)
+        N.hodlr_solve(M, bd, x, N.DAFMM_MIXED)
+        with pytest.raises(N.DafmmError) as e:
+            N.hodlr_sync(M)
+        assert e.value.code == N.DAFMM_ETIMEOUT
+        N.hodlr_solve(M, bd, x, N.DAFMM_FP64)
+        N.hodlr_sync(M)
+        assert _rel(x.cpu().numpy(), ref) < 1e-10
+    finally:
+        N.hodlr_destroy(M)
+
+
 def _solve(N, op, f, **kw):
     x = torch.zeros(op.N, dtype=torch.complex128, device="cuda")
     rc, st, hist = N.gmres_solve(op.ops, torch.as_tensor(f, device="cuda"), x, **kw)

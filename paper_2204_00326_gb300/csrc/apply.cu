@@ -357,6 +357,69 @@ struct Acc {
     }
 };
 
+// Complex128 in the single-right-hand-side launch is carried in float pairs
+// (hi + lo, about 48 significant bits): FP64 instructions issue at 1/64 of
+// the FP32 rate on GB300, so the products and sums of a chunk run in FP32
+// with exact error terms (double-float arithmetic), and rows are rounded to
+// double when they are written.  Matrices come as float4 {re hi, im hi,
+// re lo, im lo} (the same 16 bytes as a double2); inputs are split when a
+// chunk's gather is committed.
+template <>
+struct Acc<double> {
+    float rh[2][4], rl[2][4], ih[2][4], il[2][4];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) rh[s][k] = rl[s][k] = ih[s][k] = il[s][k] = 0.f;
+    }
+};
+
+// (sh, sl) += a b for float pairs a = ah + al, b = bh + bl: the rounding
+// error of ah bh exactly (FMA), the cross terms, and a two-sum into sh whose
+// error goes to sl.  Explicitly rounded operations keep the compiler from
+// contracting the error-free steps.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float t = __fadd_rn(sh, p);
+    const float v = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, v)), __fsub_rn(p, v));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// (re, im) += m x for complex float pairs {re hi, im hi, re lo, im lo}.
+__device__ __forceinline__ void df_cmac(float& rh, float& rl, float& ih, float& il, float4 m, float4 x)
+{
+    df_mac(rh, rl, m.x, m.z, x.x, x.z);
+    df_mac(rh, rl, -m.y, -m.w, x.y, x.w);
+    df_mac(ih, il, m.x, m.z, x.y, x.w);
+    df_mac(ih, il, m.y, m.w, x.x, x.z);
+}
+
+// A gathered input as it is staged for chunk_mac: complex128 split into a
+// float pair (in the 16 bytes of its double2), complex64 as it is.
+template <typename T>
+__device__ __forceinline__ typename V2<T>::t stage_x(typename V2<T>::t v)
+{
+    if constexpr (sizeof(T) == 8) {
+        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+        union {
+            float4 f;
+            double2 d;
+        } u;
+        u.f = make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+        return u.d;
+    } else {
+        return v;
+    }
+}
+
 // Multiply one chunk held in shared memory into the accumulators.
 // complex64: lane handles row pairs (2p, 2p+1) with 16-byte loads, p = lane %
 // NP (+32); complex128: lane handles rows i = lane % ro (+32k).  When the
@@ -416,62 +479,42 @@ __device__ __forceinline__ void chunk_mac(Acc<T>& acc, const typename V2<T>::t* 
             }
         }
     } else {
+        // float pairs (see Acc<double>): M and xs hold float4 entries
+        const float4* M4 = (const float4*)M;
+        const float4* X4 = (const float4*)xs;
         if (ro <= 32) {
-            // four column streams per lane (sets 0/1, slots 0/1); slot 1 is
-            // folded into slot 0 at the end, so it is zero between calls
+            // two column streams per lane (sets 0/1)
             const int JP = 32 / ro, i = lane % ro, jp = lane / ro;
             if (jp >= JP) return;
-            const double2* Mi = M + i;
+            const float4* Mi = M4 + i;
             int j = jp;
-            for (; j + 3 * JP < ncol; j += 4 * JP) {
-                const double2 m0 = Mi[j * ld], m1 = Mi[(j + JP) * ld], m2 = Mi[(j + 2 * JP) * ld], m3 = Mi[(j + 3 * JP) * ld];
-                const double2 x0 = xs[j], x1 = xs[j + JP], x2 = xs[j + 2 * JP], x3 = xs[j + 3 * JP];
-                acc.r[0][0] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][0]));
-                acc.i[0][0] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][0]));
-                acc.r[1][0] = fma(m1.x, x1.x, fma(-m1.y, x1.y, acc.r[1][0]));
-                acc.i[1][0] = fma(m1.x, x1.y, fma(m1.y, x1.x, acc.i[1][0]));
-                acc.r[0][1] = fma(m2.x, x2.x, fma(-m2.y, x2.y, acc.r[0][1]));
-                acc.i[0][1] = fma(m2.x, x2.y, fma(m2.y, x2.x, acc.i[0][1]));
-                acc.r[1][1] = fma(m3.x, x3.x, fma(-m3.y, x3.y, acc.r[1][1]));
-                acc.i[1][1] = fma(m3.x, x3.y, fma(m3.y, x3.x, acc.i[1][1]));
+            for (; j + JP < ncol; j += 2 * JP) {
+                const float4 m0 = Mi[j * ld], m1 = Mi[(j + JP) * ld];
+                const float4 x0 = X4[j], x1 = X4[j + JP];
+                df_cmac(acc.rh[0][0], acc.rl[0][0], acc.ih[0][0], acc.il[0][0], m0, x0);
+                df_cmac(acc.rh[1][0], acc.rl[1][0], acc.ih[1][0], acc.il[1][0], m1, x1);
             }
-            for (; j < ncol; j += JP) {
-                const double2 m0 = Mi[j * ld];
-                const double2 x0 = xs[j];
-                acc.r[0][0] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][0]));
-                acc.i[0][0] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][0]));
-            }
-#pragma unroll
-            for (int s = 0; s < 2; s++) {
-                acc.r[s][0] += acc.r[s][1];
-                acc.i[s][0] += acc.i[s][1];
-                acc.r[s][1] = acc.i[s][1] = 0;
-            }
+            if (j < ncol) df_cmac(acc.rh[0][0], acc.rl[0][0], acc.ih[0][0], acc.il[0][0], Mi[j * ld], X4[j]);
         } else {
             // rows lane + 32 k; even columns into set 0, odd into set 1
             const int nck = (ro + 31) / 32;
             int j = 0;
             for (; j + 1 < ncol; j += 2) {
-                const double2 x0 = xs[j], x1 = xs[j + 1];
+                const float4 x0 = X4[j], x1 = X4[j + 1];
 #pragma unroll
                 for (int k = 0; k < 4; k++)
                     if (k < nck && k * 32 + lane < ro) {
-                        const double2 m0 = M[j * ld + k * 32 + lane], m1 = M[(j + 1) * ld + k * 32 + lane];
-                        acc.r[0][k] = fma(m0.x, x0.x, fma(-m0.y, x0.y, acc.r[0][k]));
-                        acc.i[0][k] = fma(m0.x, x0.y, fma(m0.y, x0.x, acc.i[0][k]));
-                        acc.r[1][k] = fma(m1.x, x1.x, fma(-m1.y, x1.y, acc.r[1][k]));
-                        acc.i[1][k] = fma(m1.x, x1.y, fma(m1.y, x1.x, acc.i[1][k]));
+                        const float4 m0 = M4[j * ld + k * 32 + lane], m1 = M4[(j + 1) * ld + k * 32 + lane];
+                        df_cmac(acc.rh[0][k], acc.rl[0][k], acc.ih[0][k], acc.il[0][k], m0, x0);
+                        df_cmac(acc.rh[1][k], acc.rl[1][k], acc.ih[1][k], acc.il[1][k], m1, x1);
                     }
             }
             if (j < ncol) {
-                const double2 x0 = xs[j];
+                const float4 x0 = X4[j];
 #pragma unroll
                 for (int k = 0; k < 4; k++)
-                    if (k < nck && k * 32 + lane < ro) {
-                        const double2 m = M[j * ld + k * 32 + lane];
-                        acc.r[0][k] = fma(m.x, x0.x, fma(-m.y, x0.y, acc.r[0][k]));
-                        acc.i[0][k] = fma(m.x, x0.y, fma(m.y, x0.x, acc.i[0][k]));
-                    }
+                    if (k < nck && k * 32 + lane < ro)
+                        df_cmac(acc.rh[0][k], acc.rl[0][k], acc.ih[0][k], acc.il[0][k], M4[j * ld + k * 32 + lane], x0);
             }
         }
     }
@@ -483,11 +526,17 @@ template <typename T>
 __device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typename V2<T>::t* dst, bool to_y, int accumulate)
 {
     using C = typename V2<T>::t;
-    // combine the two independent sets
+    // combine the two independent sets (complex128: rounded to double here)
+    T r0[4], i0[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        acc.r[0][k] += acc.r[1][k];
-        acc.i[0][k] += acc.i[1][k];
+        if constexpr (sizeof(T) == 8) {
+            r0[k] = ((double)acc.rh[0][k] + (double)acc.rl[0][k]) + ((double)acc.rh[1][k] + (double)acc.rl[1][k]);
+            i0[k] = ((double)acc.ih[0][k] + (double)acc.il[0][k]) + ((double)acc.ih[1][k] + (double)acc.il[1][k]);
+        } else {
+            r0[k] = acc.r[0][k] + acc.r[1][k];
+            i0[k] = acc.i[0][k] + acc.i[1][k];
+        }
     }
     auto put = [&](int row, T re, T im) {
         C* q = dst + row;
@@ -509,23 +558,23 @@ __device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typenam
             for (int k = 0; k < 2; k++)
                 for (int q = 1; q < JP; q++) {
                     const int src = (lane + q * NP) & 31;
-                    const float tr = __shfl_sync(0xffffffffu, acc.r[0][k], src);
-                    const float ti = __shfl_sync(0xffffffffu, acc.i[0][k], src);
+                    const float tr = __shfl_sync(0xffffffffu, r0[k], src);
+                    const float ti = __shfl_sync(0xffffffffu, i0[k], src);
                     if (jp == 0) {
-                        acc.r[0][k] += tr;
-                        acc.i[0][k] += ti;
+                        r0[k] += tr;
+                        i0[k] += ti;
                     }
                 }
             if (jp == 0) {
-                put(2 * p, acc.r[0][0], acc.i[0][0]);
-                if (2 * p + 1 < ro) put(2 * p + 1, acc.r[0][1], acc.i[0][1]);
+                put(2 * p, r0[0], i0[0]);
+                if (2 * p + 1 < ro) put(2 * p + 1, r0[1], i0[1]);
             }
         } else {
-            put(2 * lane, acc.r[0][0], acc.i[0][0]);
-            if (2 * lane + 1 < ro) put(2 * lane + 1, acc.r[0][1], acc.i[0][1]);
+            put(2 * lane, r0[0], i0[0]);
+            if (2 * lane + 1 < ro) put(2 * lane + 1, r0[1], i0[1]);
             if (lane + 32 < NP) {
-                put(2 * lane + 64, acc.r[0][2], acc.i[0][2]);
-                if (2 * lane + 65 < ro) put(2 * lane + 65, acc.r[0][3], acc.i[0][3]);
+                put(2 * lane + 64, r0[2], i0[2]);
+                if (2 * lane + 65 < ro) put(2 * lane + 65, r0[3], i0[3]);
             }
         }
     } else {
@@ -533,18 +582,18 @@ __device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typenam
             const int JP = 32 / ro, i = lane % ro, jp = lane / ro;
             for (int q = 1; q < JP; q++) {
                 const int src = (lane + q * ro) & 31;
-                const double tr = __shfl_sync(0xffffffffu, acc.r[0][0], src);
-                const double ti = __shfl_sync(0xffffffffu, acc.i[0][0], src);
+                const double tr = __shfl_sync(0xffffffffu, r0[0], src);
+                const double ti = __shfl_sync(0xffffffffu, i0[0], src);
                 if (jp == 0) {
-                    acc.r[0][0] += tr;
-                    acc.i[0][0] += ti;
+                    r0[0] += tr;
+                    i0[0] += ti;
                 }
             }
-            if (jp == 0) put(i, acc.r[0][0], acc.i[0][0]);
+            if (jp == 0) put(i, r0[0], i0[0]);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                if (k * 32 + lane < ro) put(k * 32 + lane, acc.r[0][k], acc.i[0][k]);
+                if (k * 32 + lane < ro) put(k * 32 + lane, r0[k], i0[k]);
         }
     }
 }
@@ -802,7 +851,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
 #pragma unroll
         for (int k = 0; k < kMaxPrefetch; k++) {
             const int t = lane + 32 * k;
-            if (t < ncol) xs[t] = xr[k];
+            if (t < ncol) xs[t] = stage_x<T>(xr[k]);
         }
         // records of the chunk after next; the next chunk's inputs when its passes are known complete
         int4 fa = make_int4(-1, -1, 0, 0), fb = make_int4(0, 0, 0, 0);
@@ -1393,13 +1442,24 @@ void upload_bsr(BsrHost& h, BsrDev& d)
     // two spare entries: a bulk copy rounds its window out to 16-byte words
     dev_alloc((double2**)&d.m64, sizeof(double2) * (n + 2));
     dev_alloc((float2**)&d.m32, sizeof(float2) * (n + 4));
+    dev_alloc((float4**)&d.mdf, sizeof(float4) * (n + 2));
     CK(cudaMemset(d.m64, 0, sizeof(double2) * (n + 2)));
     CK(cudaMemset(d.m32, 0, sizeof(float2) * (n + 4)));
+    CK(cudaMemset(d.mdf, 0, sizeof(float4) * (n + 2)));
     if (n) {
         CK(cudaMemcpy(d.m64, h.mats.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
         std::vector<float2> f(n);
         for (size_t k = 0; k < n; k++) f[k] = make_float2((float)h.mats[k].real(), (float)h.mats[k].imag());
         CK(cudaMemcpy(d.m32, f.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+        std::vector<float2>().swap(f);
+        // each double as hi + lo: hi its nearest float, lo the nearest float of the rest
+        std::vector<float4> df(n);
+        for (size_t k = 0; k < n; k++) {
+            const double re = h.mats[k].real(), im = h.mats[k].imag();
+            const float rh = (float)re, ih = (float)im;
+            df[k] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+        }
+        CK(cudaMemcpy(d.mdf, df.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
     }
     std::vector<cd>().swap(h.mats);
 }
@@ -1413,6 +1473,7 @@ void free_bsr(BsrDev& d)
     cudaFree(d.moff);
     cudaFree(d.m64);
     cudaFree(d.m32);
+    cudaFree(d.mdf);
     d = BsrDev();
 }
 
@@ -1883,7 +1944,8 @@ PassArgs<T> fused_pass_args(const Tree& t, const OpsDev& d, const FBufs<T>& b, c
     a.rbase = g.rbase[p];
     a.cbase = g.cbase[p];
     a.xmap = g.xmap[p];
-    a.mats = (const C*)(sizeof(T) == 8 ? bs.m64 : bs.m32);
+    // complex128: the float-pair copy (16 bytes an entry, like double2), see chunk_mac
+    a.mats = (const C*)(sizeof(T) == 8 ? bs.mdf : bs.m32);
     if (pr.kind == 0 || pr.kind == 3) {
         if (nu == t.L || pr.kind == 3)
             a.xd = (const double2*)v;

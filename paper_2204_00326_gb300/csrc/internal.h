@@ -111,6 +111,7 @@ struct BsrDev {
     int* rowptr = nullptr;
     void* m64 = nullptr;  // double2 blocks
     void* m32 = nullptr;  // float2 blocks
+    void* mdf = nullptr;  // float4 blocks {re hi, im hi, re lo, im lo}: complex128 as float pairs
 };
 
 // Everything the matvec needs, produced on the host by the NCA setup.

@@ -111,8 +111,6 @@ struct dafmm_hodlr {
     void* s_buf = nullptr;   // s per node, two parity halves of 2 rmax x N / leaf
     void* xw = nullptr;      // complex64 work vector (mixed precision)
     long sbuf_half = 0;      // entries of one parity half of s_buf
-    int* cnt = nullptr;      // per-node arrival counters of the apply launch
-    long ncnt = 0;
     unsigned* bar = nullptr;  // grid barrier: arrivals, exits
     int* err = nullptr;       // set when a wait of the apply gave up
     int ncta = 1;             // CTAs of the apply launch
@@ -234,10 +232,14 @@ __device__ __forceinline__ C cmul(C a, C b)
 //   1. x = D^{-1} b on its leaves;
 //   then for every level l from the leaves up (n = N >> l, halves of h = n/2):
 //   2. partial sums of t = W x over its segments (min(E, h) unknowns each);
-//   3. the last CTA to finish a node (an arrival counter per node) sums the
-//      partials into t and forms s = S^{-1} t for that node;
-//   4. grid barrier (every node's s is written);
-//   5. x -= Ut s on its unknowns.
+//   3. each segment's share of s = S^{-1} t (S^{-1} t is linear in t, and a
+//      segment adds to one half of t): the half's columns of S^{-1} times
+//      the segment's partial sums;
+//   4. grid barrier (every share is written; not needed at levels whose
+//      nodes each lie in one CTA);
+//   5. s of each segment's half as the sum of its node's shares (a fixed
+//      order, so results do not depend on timing), then x -= Ut s on its
+//      unknowns.
 // Steps 5 and 2 of the next level touch only the CTA's own unknowns, so one
 // barrier per level suffices.  Every wait has a time limit, after which the
 // launch sets the handle's error flag and returns.
@@ -256,9 +258,8 @@ struct HArgs {
     double2* xout;       // result (complex128)
     C* x;                // work vector (xout itself in complex128)
     C* part;             // partial sums, [q][segment]
-    C* sbuf;             // s per node, two buffers by level parity: [parity][node][2 r]
+    C* sbuf;             // shares of s per segment, two buffers by level parity: [parity][segment][2 r]
     long sbuf_half;      // entries per parity buffer
-    int* cnt;            // arrival counters per node (zero between launches)
     unsigned* bar;       // [0] barrier arrivals, [1] exits
     int* err;
     const C* R[kHodlrMaxLevels];  // r x N
@@ -361,7 +362,6 @@ __global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant_
     using C = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char hsm[];
     C* sh = (C*)hsm;
-    __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kW = kHT / 32;
     const long E = a.E, e0 = (long)blockIdx.x * E;
@@ -435,63 +435,28 @@ __global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant_
                 }
             }
         }
-        __threadfence();
-        __syncthreads();
-        // 3. s = S^{-1} t for every node this CTA completes
-        C* sb = a.sbuf + (size_t)(l & 1) * a.sbuf_half;
-        const long nodes_here = E >= n ? E / n : 1, node0 = e0 / n;
-        for (long nd = node0; nd < node0 + nodes_here; nd++) {
-            if (E < n) {
-                if (tid == 0) {
-                    const int last = atomicAdd(&a.cnt[nd], 1) == (int)(n / E) - 1;
-                    if (last) a.cnt[nd] = 0;
-                    __threadfence();
-                    s_last = last;
-                }
-                __syncthreads();
-                if (!s_last) continue;
-            }
-            // t[0..r): half 2 (V12 x2); t[r..2r): half 1 (V21 x1).  Rows are
-            // split over p consecutive lanes (p a power of two, 2r p <= kHT
-            // where possible) so that every thread's loads go out together.
-            const int R2 = 2 * r;
-            int p = 1;
-            while (p < 32 && 2 * p * R2 <= kHT) p *= 2;
-            const int rpp = kHT / p, npass = (R2 + rpp - 1) / rpp, piece = tid % p;
-            const long gh = h / m, g1 = nd * n / m;
-            for (int pass = 0; pass < npass; pass++) {
-                const int aa = pass * rpp + tid / p;
-                T sr = 0, si = 0;
-                if (aa < R2) {
-                    const int q = aa < r ? aa : aa - r;
-                    const C* P = a.part + (size_t)q * nslots + (aa < r ? g1 + gh : g1);
-#pragma unroll 8
-                    for (long k = piece; k < gh; k += p) {
-                        const C v = __ldcg(P + k);
-                        sr += v.x;
-                        si += v.y;
-                    }
-                }
-                for (int o = p / 2; o > 0; o >>= 1) {
-                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                    si += __shfl_xor_sync(0xffffffffu, si, o);
-                }
-                if (aa < R2 && piece == 0) {
-                    C o;
-                    o.x = sr;
-                    o.y = si;
-                    sh[aa] = o;
-                }
-            }
+        __syncthreads();  // this CTA's partials are written
+        // 3. each segment's share of s = S^{-1} t: t takes half 2's sums in rows [0, r) and
+        //    half 1's in [r, 2r), so segment g of half hh adds S[:, cols] part_g with cols
+        //    [0, r) (hh = 1) or [r, 2r) (hh = 0).  Rows of S are split over p consecutive lanes.
+        const int R2 = 2 * r;
+        C* cb = a.sbuf + (size_t)(l & 1) * a.sbuf_half;  // shares: [segment][2 r]
+        int p = 1;
+        while (p < 32 && 2 * p * R2 <= kHT) p *= 2;
+        const int rpp = kHT / p, npass = (R2 + rpp - 1) / rpp, piece = tid % p;
+        for (long s0 = e0; s0 < e0 + E; s0 += m) {
+            const long g = s0 / m, nd = s0 / n;
+            const int colb = (s0 - nd * n) >= h ? 0 : r;
+            for (int q = tid; q < r; q += kHT) sh[q] = a.part[(size_t)q * nslots + g];
             __syncthreads();
-            const C* Sn = a.S[l] + (size_t)nd * 4 * r * r;
-            const int cols = (R2 + p - 1) / p;
+            const C* Sn = a.S[l] + (size_t)nd * 4 * r * r + colb;
+            const int cols = (r + p - 1) / p;
             for (int pass = 0; pass < npass; pass++) {
                 const int aa = pass * rpp + tid / p;
                 T sr = 0, si = 0;
                 if (aa < R2) {
                     const C* row = Sn + (size_t)aa * R2;
-                    const int b1 = min(R2, (piece + 1) * cols);
+                    const int b1 = min(r, (piece + 1) * cols);
 #pragma unroll 8
                     for (int bb = piece * cols; bb < b1; bb++) cmac(sr, si, row[bb], sh[bb]);
                 }
@@ -503,28 +468,60 @@ __global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant_
                     C o;
                     o.x = sr;
                     o.y = si;
-                    sb[(size_t)nd * 2 * r + aa] = o;
+                    cb[(size_t)g * R2 + aa] = o;
                 }
             }
             __syncthreads();
         }
-        // 4. every node's s is written
-        nb++;
-        if (!h_barrier(&a.bar[0], nb * (unsigned)a.ncta + (unsigned)a.extra, a.err)) {
-            ok = false;
-            break;
+        // 4. every share is written; a level whose nodes each lie in one CTA reads only its own
+        if (E < n) {
+            nb++;
+            if (!h_barrier(&a.bar[0], nb * (unsigned)a.ncta + (unsigned)a.extra, a.err)) {
+                ok = false;
+                break;
+            }
+        } else {
+            __threadfence_block();
+            __syncthreads();
         }
-        // 5. x -= Ut s on this CTA's unknowns, one segment (one half's s, staged
-        // in shared memory) at a time; a segment shorter than the CTA splits
-        // the sum over q between tpe threads per unknown
+        // 5. per segment: s of its half = the sum of the node's shares (a fixed order: rows q
+        //    over p2 lanes, each lane its strided subset, then a shuffle tree), staged in shared
+        //    memory; then x -= Ut s on the segment, the sum over q split between tpe threads
+        //    per unknown when the segment is shorter than the CTA
         const C* U = a.U[l];
         const int tpe = m >= kHT ? 1 : (int)(kHT / m);
         C* red = sh + 2 * r;  // tpe x m partial sums (tpe > 1)
+        int p2 = 1;
+        while (p2 < 32 && 2 * p2 * r <= kHT) p2 *= 2;
+        const int rpp2 = kHT / p2, npass2 = (r + rpp2 - 1) / rpp2, piece2 = tid % p2;
         for (long s0 = e0; s0 < e0 + E; s0 += m) {
             const long nd = s0 / n;
-            const C* sv = sb + (size_t)nd * 2 * r + ((s0 - nd * n) >= h ? r : 0);
+            const int hoff = (s0 - nd * n) >= h ? r : 0;
+            const long ga = nd * n / m, gn = n / m;  // the node's segments [ga, ga + gn)
             __syncthreads();
-            for (int q = tid; q < r; q += kHT) sh[q] = __ldcg(sv + q);
+            for (int pass = 0; pass < npass2; pass++) {
+                const int q = pass * rpp2 + tid / p2;
+                T sr = 0, si = 0;
+                if (q < r) {
+                    const C* P = cb + (size_t)ga * R2 + hoff + q;
+#pragma unroll 8
+                    for (long k = piece2; k < gn; k += p2) {
+                        const C v = __ldcg(P + (size_t)k * R2);
+                        sr += v.x;
+                        si += v.y;
+                    }
+                }
+                for (int o = p2 / 2; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (q < r && piece2 == 0) {
+                    C o;
+                    o.x = sr;
+                    o.y = si;
+                    sh[q] = o;
+                }
+            }
             __syncthreads();
             const int g = tid / (int)min(m, (long)kHT);
             for (long k = tid % min(m, (long)kHT); k < m; k += min(m, (long)kHT)) {
@@ -605,7 +602,6 @@ void apply(const dafmm_hodlr& h, const double2* b, double2* xout, cudaStream_t s
     a.part = (C*)h.t_part;
     a.sbuf = (C*)h.s_buf;
     a.sbuf_half = h.sbuf_half;
-    a.cnt = h.cnt;
     a.bar = h.bar;
     a.err = h.err;
     for (int l = 0; l < h.H; l++) {
@@ -672,8 +668,7 @@ int hodlr_check(const dafmm_hodlr* h, cudaStream_t s)
     int flag = 0;
     CK(cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (!flag) return DAFMM_OK;
-    // a launch that gave up may have left node counters armed
-    CK(cudaMemset(h->cnt, 0, sizeof(int) * (size_t)h->ncnt));
+    // a launch that gave up may have left the barrier armed
     CK(cudaMemset(h->bar, 0, 2 * sizeof(unsigned)));
     CK(cudaMemset(h->err, 0, sizeof(int)));
     return DAFMM_ETIMEOUT;
@@ -831,15 +826,13 @@ dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf)
         }
         const long nl = std::max<long>(N / h->leaf, 1);
         h->sbuf_half = 2L * std::max(1, h->rmax) * nl;
-        h->ncnt = nl;
         if (cudaMalloc(&h->t_part, sizeof(double2) * std::max(1, h->rmax) * nl) != cudaSuccess ||
             cudaMalloc(&h->s_buf, sizeof(double2) * 2 * h->sbuf_half) != cudaSuccess ||
-            cudaMalloc(&h->xw, sizeof(float2) * N) != cudaSuccess || cudaMalloc(&h->cnt, sizeof(int) * nl) != cudaSuccess ||
+            cudaMalloc(&h->xw, sizeof(float2) * N) != cudaSuccess ||
             cudaMalloc(&h->bar, 2 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&h->err, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             fail(DAFMM_ENOMEM, "device allocation for the HODLR work buffers failed");
         }
-        CK(cudaMemset(h->cnt, 0, sizeof(int) * nl));
         CK(cudaMemset(h->bar, 0, 2 * sizeof(unsigned)));
         CK(cudaMemset(h->err, 0, sizeof(int)));
         h->ncta_cap = apply_capacity(*h);
@@ -869,7 +862,6 @@ void hodlr_free(dafmm_hodlr* h)
     cudaFree(h->t_part);
     cudaFree(h->s_buf);
     cudaFree(h->xw);
-    cudaFree(h->cnt);
     cudaFree(h->bar);
     cudaFree(h->err);
     delete h;

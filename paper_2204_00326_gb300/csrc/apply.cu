@@ -244,6 +244,54 @@ __device__ __forceinline__ int deps_wait(const Sched& sc, const int* done, unsig
     return 1;
 }
 
+// Complex128 coefficients of the single-right-hand-side launch are kept as
+// float pairs {re hi, im hi, re lo, im lo} in the 16 bytes of a double2
+// (double-float arithmetic; see Acc<double>).
+__device__ __forceinline__ float4 as_df(double2 d)
+{
+    union {
+        double2 d;
+        float4 f;
+    } u;
+    u.d = d;
+    return u.f;
+}
+__device__ __forceinline__ double2 df_bits(float4 f)
+{
+    union {
+        double2 d;
+        float4 f;
+    } u;
+    u.f = f;
+    return u.d;
+}
+
+// (h, l) = a + b for float pairs (two-sum of the high words, the low words
+// and the error added, renormalised).
+__device__ __forceinline__ void df_add(float& h, float& l, float ah, float al, float bh, float bl)
+{
+    const float s = __fadd_rn(ah, bh);
+    const float v = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(ah, __fsub_rn(s, v)), __fsub_rn(bh, v)), __fadd_rn(al, bl));
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+__device__ __forceinline__ float4 df4_add(float4 a, float4 b)
+{
+    float4 r;
+    df_add(r.x, r.z, a.x, a.z, b.x, b.z);
+    df_add(r.y, r.w, a.y, a.w, b.y, b.w);
+    return r;
+}
+
+// A double as a float pair: hi its nearest float, lo the nearest float of the rest.
+__device__ __forceinline__ double2 df_split(double2 v)
+{
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return df_bits(make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih)));
+}
+
 // Partial slot of the warp share of phase k that starts at chunk c.
 __device__ __forceinline__ int share_slot(const Sched& sc, int k, int c) { return sc.sbase[k] + (c - sc.base[k]) / sc.kpw[k]; }
 
@@ -288,14 +336,22 @@ __device__ __forceinline__ bool own_row(typename V2<T>::t* y, const typename V2<
     __syncwarp();  // lane 0's acquire, and the owner's own stores to y, come before every lane's reads
     for (int i = lane; i < ro; i += 32) {
         C o = y[i];
-        T sr = o.x, si = o.y;
-        for (int c = next_slot(c0, base, kpw); c < c1; c = next_slot(c, base, kpw)) {
-            const C p = __ldcg(&P[(size_t)share_slot(sc, k, c) * Pld + i]);
-            sr += p.x;
-            si += p.y;
+        if constexpr (sizeof(T) == 8) {
+            // float pairs (double-float)
+            float4 a = as_df(o);
+            for (int c = next_slot(c0, base, kpw); c < c1; c = next_slot(c, base, kpw))
+                a = df4_add(a, as_df(__ldcg(&P[(size_t)share_slot(sc, k, c) * Pld + i])));
+            o = df_bits(a);
+        } else {
+            T sr = o.x, si = o.y;
+            for (int c = next_slot(c0, base, kpw); c < c1; c = next_slot(c, base, kpw)) {
+                const C p = __ldcg(&P[(size_t)share_slot(sc, k, c) * Pld + i]);
+                sr += p.x;
+                si += p.y;
+            }
+            o.x = sr;
+            o.y = si;
         }
-        o.x = sr;
-        o.y = si;
         y[i] = o;
     }
     return true;
@@ -326,7 +382,15 @@ __device__ __forceinline__ void gather_val(const GroupArgs<T>& g, const int4& a,
         if (t < a.z) {
             const int ix = xi[k];
             C v;
-            if (pa.xd) {
+            if constexpr (sizeof(T) == 8) {
+                // complex128: float pairs (the input split, coefficients stored so)
+                if (pa.xd) {
+                    v = df_split(pa.xd[ix]);
+                } else {
+                    v = __ldcg(pa.x + ix);
+                    if (pa.x2) v = df_bits(df4_add(as_df(v), as_df(__ldcg(pa.x2 + ix))));
+                }
+            } else if (pa.xd) {
                 const double2 d = pa.xd[ix];
                 v.x = (T)d.x;
                 v.y = (T)d.y;
@@ -360,10 +424,10 @@ struct Acc {
 // Complex128 in the single-right-hand-side launch is carried in float pairs
 // (hi + lo, about 48 significant bits): FP64 instructions issue at 1/64 of
 // the FP32 rate on GB300, so the products and sums of a chunk run in FP32
-// with exact error terms (double-float arithmetic), and rows are rounded to
-// double when they are written.  Matrices come as float4 {re hi, im hi,
-// re lo, im lo} (the same 16 bytes as a double2); inputs are split when a
-// chunk's gather is committed.
+// with exact error terms (double-float arithmetic); the pass outputs stay
+// float pairs too (the leaf kernel rounds them to double).  Matrices come as
+// float4 {re hi, im hi, re lo, im lo} (the same 16 bytes as a double2); the
+// input vector is split when it is gathered.
 template <>
 struct Acc<double> {
     float rh[2][4], rl[2][4], ih[2][4], il[2][4];
@@ -400,24 +464,6 @@ __device__ __forceinline__ void df_cmac(float& rh, float& rl, float& ih, float& 
     df_mac(rh, rl, -m.y, -m.w, x.y, x.w);
     df_mac(ih, il, m.x, m.z, x.y, x.w);
     df_mac(ih, il, m.y, m.w, x.x, x.z);
-}
-
-// A gathered input as it is staged for chunk_mac: complex128 split into a
-// float pair (in the 16 bytes of its double2), complex64 as it is.
-template <typename T>
-__device__ __forceinline__ typename V2<T>::t stage_x(typename V2<T>::t v)
-{
-    if constexpr (sizeof(T) == 8) {
-        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-        union {
-            float4 f;
-            double2 d;
-        } u;
-        u.f = make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
-        return u.d;
-    } else {
-        return v;
-    }
 }
 
 // Multiply one chunk held in shared memory into the accumulators.
@@ -522,35 +568,65 @@ __device__ __forceinline__ void chunk_mac(Acc<T>& acc, const typename V2<T>::t* 
 
 // Sum the accumulators over the lane groups and write the row (to y when the
 // chunk range covers the whole row, else to the partial slot P[pslot]).
+// Complex128 rows are written as float pairs (double-float, see Acc<double>).
+__device__ __forceinline__ void flush_row_df(Acc<double>& acc, int ro, int lane, double2* dst, bool to_y, int accumulate)
+{
+    float h[4], l[4], ih[4], il[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        df_add(h[k], l[k], acc.rh[0][k], acc.rl[0][k], acc.rh[1][k], acc.rl[1][k]);
+        df_add(ih[k], il[k], acc.ih[0][k], acc.il[0][k], acc.ih[1][k], acc.il[1][k]);
+    }
+    auto put = [&](int row, float rh, float rl, float jh, float jl) {
+        float4 v = make_float4(rh, jh, rl, jl);
+        if (to_y && accumulate) v = df4_add(v, as_df(dst[row]));
+        dst[row] = df_bits(v);
+    };
+    if (ro <= 32) {
+        const int JP = 32 / ro, i = lane % ro, jp = lane / ro;
+        for (int q = 1; q < JP; q++) {
+            const int src = (lane + q * ro) & 31;
+            const float th = __shfl_sync(0xffffffffu, h[0], src), tl = __shfl_sync(0xffffffffu, l[0], src);
+            const float uh = __shfl_sync(0xffffffffu, ih[0], src), ul = __shfl_sync(0xffffffffu, il[0], src);
+            if (jp == 0) {
+                df_add(h[0], l[0], h[0], l[0], th, tl);
+                df_add(ih[0], il[0], ih[0], il[0], uh, ul);
+            }
+        }
+        if (jp == 0) put(i, h[0], l[0], ih[0], il[0]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (k * 32 + lane < ro) put(k * 32 + lane, h[k], l[k], ih[k], il[k]);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typename V2<T>::t* dst, bool to_y, int accumulate)
 {
     using C = typename V2<T>::t;
-    // combine the two independent sets (complex128: rounded to double here)
-    T r0[4], i0[4];
+    if constexpr (sizeof(T) == 8) {
+        flush_row_df(acc, ro, lane, dst, to_y, accumulate);
+    } else {
+        // combine the two independent sets
+        T r0[4], i0[4];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        if constexpr (sizeof(T) == 8) {
-            r0[k] = ((double)acc.rh[0][k] + (double)acc.rl[0][k]) + ((double)acc.rh[1][k] + (double)acc.rl[1][k]);
-            i0[k] = ((double)acc.ih[0][k] + (double)acc.il[0][k]) + ((double)acc.ih[1][k] + (double)acc.il[1][k]);
-        } else {
+        for (int k = 0; k < 4; k++) {
             r0[k] = acc.r[0][k] + acc.r[1][k];
             i0[k] = acc.i[0][k] + acc.i[1][k];
         }
-    }
-    auto put = [&](int row, T re, T im) {
-        C* q = dst + row;
-        if (to_y && accumulate) {
-            const C o = *q;
-            re += o.x;
-            im += o.y;
-        }
-        C r;
-        r.x = re;
-        r.y = im;
-        *q = r;
-    };
-    if constexpr (sizeof(T) == 4) {
+        auto put = [&](int row, T re, T im) {
+            C* q = dst + row;
+            if (to_y && accumulate) {
+                const C o = *q;
+                re += o.x;
+                im += o.y;
+            }
+            C r;
+            r.x = re;
+            r.y = im;
+            *q = r;
+        };
         const int NP = (ro + 1) >> 1;
         if (NP <= 32) {
             const int JP = 32 / NP, p = lane % NP, jp = lane / NP;
@@ -576,24 +652,6 @@ __device__ __forceinline__ void flush_row(Acc<T>& acc, int ro, int lane, typenam
                 put(2 * lane + 64, r0[2], i0[2]);
                 if (2 * lane + 65 < ro) put(2 * lane + 65, r0[3], i0[3]);
             }
-        }
-    } else {
-        if (ro <= 32) {
-            const int JP = 32 / ro, i = lane % ro, jp = lane / ro;
-            for (int q = 1; q < JP; q++) {
-                const int src = (lane + q * ro) & 31;
-                const double tr = __shfl_sync(0xffffffffu, r0[0], src);
-                const double ti = __shfl_sync(0xffffffffu, i0[0], src);
-                if (jp == 0) {
-                    r0[0] += tr;
-                    i0[0] += ti;
-                }
-            }
-            if (jp == 0) put(i, r0[0], i0[0]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (k * 32 + lane < ro) put(k * 32 + lane, r0[k], i0[k]);
         }
     }
 }
@@ -662,16 +720,23 @@ __device__ __forceinline__ bool bulk_finish(typename V2<T>::t* y, const typename
     if (!last) return false;
     __syncwarp();
     for (int i = lane; i < ro; i += 32) {
-        T sr = 0, si = 0;
-        for (int q = 0; q < np; q++) {
-            const C p = __ldcg(&P[(size_t)(s0 + q) * Pld + i]);
-            sr += p.x;
-            si += p.y;
+        if constexpr (sizeof(T) == 8) {
+            // float pairs (double-float)
+            float4 a = as_df(__ldcg(&P[(size_t)s0 * Pld + i]));
+            for (int q = 1; q < np; q++) a = df4_add(a, as_df(__ldcg(&P[(size_t)(s0 + q) * Pld + i])));
+            y[i] = df_bits(a);
+        } else {
+            T sr = 0, si = 0;
+            for (int q = 0; q < np; q++) {
+                const C p = __ldcg(&P[(size_t)(s0 + q) * Pld + i]);
+                sr += p.x;
+                si += p.y;
+            }
+            C o;
+            o.x = sr;
+            o.y = si;
+            y[i] = o;
         }
-        C o;
-        o.x = sr;
-        o.y = si;
-        y[i] = o;
     }
     if (lane == 0) cnt[c0] = 0;
     return true;
@@ -851,7 +916,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
 #pragma unroll
         for (int k = 0; k < kMaxPrefetch; k++) {
             const int t = lane + 32 * k;
-            if (t < ncol) xs[t] = stage_x<T>(xr[k]);
+            if (t < ncol) xs[t] = xr[k];
         }
         // records of the chunk after next; the next chunk's inputs when its passes are known complete
         int4 fa = make_int4(-1, -1, 0, 0), fb = make_int4(0, 0, 0, 0);
@@ -1333,6 +1398,9 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
         const bool composed = grp == 1;
         const int* rowptr = composed ? c_rowptr : l2p_rowptr;
         if (rowptr != nullptr) {
+            // complex128: operators and locals are float pairs, multiplied in double-float
+            // (two column streams), rounded to double once at the end
+            float dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f}, eh[2] = {0.f, 0.f}, el[2] = {0.f, 0.f};
             for (int e = rowptr[leaf]; e < rowptr[leaf + 1]; e++) {
                 // composed: 16 x ri blocks on the parent level's locals (lcA + lcB); L2P: on the leaf's locals
                 const C* U = composed ? cm + c_moff[e] + i : l2p + l2p_moff[e] + i;
@@ -1349,16 +1417,29 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
                             Uj[j] = U[(j0 + j) * 16];
                             if (u2) {
                                 const C w = u2[j0 + j];
-                                uj[j].x += w.x;
-                                uj[j].y += w.y;
+                                if constexpr (sizeof(T) == 8) {
+                                    uj[j] = df_bits(df4_add(as_df(uj[j]), as_df(w)));
+                                } else {
+                                    uj[j].x += w.x;
+                                    uj[j].y += w.y;
+                                }
                             }
                         }
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        if (j0 + j < ri) cmac<T>(ar0, ai0, Uj[j], uj[j]);
-                        if (j0 + j + 1 < ri) cmac<T>(ar1, ai1, Uj[j + 1], uj[j + 1]);
-                    }
+                    for (int j = 0; j < 16; j++)
+                        if (j0 + j < ri) {
+                            if constexpr (sizeof(T) == 8)
+                                df_cmac(dh[j & 1], dl[j & 1], eh[j & 1], el[j & 1], as_df(Uj[j]), as_df(uj[j]));
+                            else if (j & 1)
+                                cmac<T>(ar1, ai1, Uj[j], uj[j]);
+                            else
+                                cmac<T>(ar0, ai0, Uj[j], uj[j]);
+                        }
                 }
+            }
+            if constexpr (sizeof(T) == 8) {
+                ar0 += ((double)dh[0] + (double)dl[0]) + ((double)dh[1] + (double)dl[1]);
+                ai0 += ((double)eh[0] + (double)el[0]) + ((double)eh[1] + (double)el[1]);
             }
         }
     }
@@ -2059,10 +2140,10 @@ void run_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const double* 
     const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
     const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
     const bool comp = far && L - 1 >= t.top;
-    const C* cm = comp ? (const C*)(sizeof(T) == 8 ? d.leafc.m64 : d.leafc.m32) : nullptr;
+    const C* cm = comp ? (const C*)(sizeof(T) == 8 ? d.leafc.mdf : d.leafc.m32) : nullptr;
     leaf_apply_kernel<T><<<(unsigned)((nleaf + kLeafPerCta - 1) / kLeafPerCta), 48 * kLeafPerCta, 0, s>>>(
         nleaf, d.nbr, nearp, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
-        l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr, nullptr,
+        l2p ? (const C*)(sizeof(T) == 8 ? l2p->mdf : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr, nullptr,
         comp ? d.leafc.rowptr : nullptr, comp ? d.leafc.col : nullptr, comp ? d.leafc.moff : nullptr, comp ? d.leafc.rin : nullptr, cm,
         comp ? d.lv[L - 1].Ri : 0, comp ? b.lc[L - 1] : nullptr, comp && L - 1 > t.top ? b.lcd[L - 1] : nullptr, (const double2*)v, d.q,
         t.prm.kappa * t.prm.kappa, (double2*)out, far ? d.fz.done : nullptr);

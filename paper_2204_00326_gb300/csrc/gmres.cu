@@ -11,8 +11,10 @@
 // restart; with mixed inner operators it is iterative refinement whose
 // correction equations are solved to a relative inner tolerance.
 //
-// Arnoldi (classical Gram-Schmidt applied twice), the Hessenberg matrix, the
-// Givens rotations and every vector update stay in FP64 on the device.  One
+// Arnoldi is classical Gram-Schmidt applied twice; the Hessenberg matrix, the
+// Givens rotations, the preconditioned basis and x stay in FP64 on the
+// device, the Arnoldi basis is complex128 in FP64 cycles and complex64 in the
+// inner cycles of mixed precision (whose target is a relative 1e-5).  One
 // Arnoldi step is three reduction kernels (the last block of each sums the
 // per-block partials in block order, so results do not depend on timing) and
 // a scaling; the host reads one residual estimate (8 bytes) per step to
@@ -71,32 +73,81 @@ __device__ bool last_block(unsigned* ticket)
     return s_last != 0;
 }
 
-// Vs[k][r] = V[r0 + r, k] for r < rows, k < nk, by 16-byte asynchronous copies
-// (all in flight at once), then wait.
-__device__ __forceinline__ void stage_tile(const double2* __restrict__ V, long N, int nk, long r0, int rows, double2* Vs)
+// Basis vectors: complex128 (FP64 cycles) or complex64 (the inner cycles of
+// mixed precision, where the correction equation is solved to ~1e-5).
+template <typename T>
+struct CT;
+template <>
+struct CT<double> {
+    using t = double2;
+};
+template <>
+struct CT<float> {
+    using t = float2;
+};
+
+template <typename C>
+__device__ __forceinline__ C cmul_t(C a, C b)
+{
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+template <typename C>
+__device__ __forceinline__ C cconjmul_t(C a, C b)  // conj(a) * b
+{
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.x * b.y - a.y * b.x;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ typename CT<T>::t from64(double2 v)
+{
+    typename CT<T>::t r;
+    r.x = (T)v.x;
+    r.y = (T)v.y;
+    return r;
+}
+
+// Vs[k][r] = V[r0 + r, k] for r < rows, k < nk, by asynchronous copies (all in
+// flight at once), then wait.
+template <typename T>
+__device__ __forceinline__ void stage_tile(const typename CT<T>::t* __restrict__ V, long N, int nk, long r0, int rows, typename CT<T>::t* Vs)
 {
     for (int e = threadIdx.x; e < nk * kCR; e += blockDim.x) {
         const int k = e / kCR, r = e - k * kCR;
         if (r < rows) {
             const unsigned dst = (unsigned)__cvta_generic_to_shared(Vs + e);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(V + (size_t)k * N + r0 + r) : "memory");
+            if constexpr (sizeof(T) == 8)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(V + (size_t)k * N + r0 + r) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(V + (size_t)k * N + r0 + r) : "memory");
         }
     }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 }
 
-// ws[r] = w[r0 + r] - sum_k Vs[k][r] h[k] (h == nullptr: no update), four
-// threads per row splitting k; rows past the end are zero.  Writes the
-// updated rows back to w when h is given.
-__device__ __forceinline__ void tile_update(const double2* Vs, int nk, const double2* hs, double2* __restrict__ w, long r0, int rows,
-                                            double2* ws)
+// ws[r] = w[r0 + r] - sum_k Vs[k][r] h[k] (hs == nullptr: no update), four
+// threads per row splitting k; rows past the end are zero.  With w64 the row
+// is read from that complex128 vector instead (and rounded to T).  Writes the
+// rows back to w when they changed (hs or w64 given).
+template <typename T>
+__device__ __forceinline__ void tile_update(const typename CT<T>::t* Vs, int nk, const typename CT<T>::t* hs, typename CT<T>::t* __restrict__ w,
+                                            const double2* __restrict__ w64, long r0, int rows, typename CT<T>::t* ws)
 {
+    using C = typename CT<T>::t;
     const int r = threadIdx.x >> 2, part = threadIdx.x & 3;  // kAT = 4 kCR
-    double2 a = make_double2(0, 0);
+    C a;
+    a.x = 0;
+    a.y = 0;
     if (hs)
         for (int k = part; k < nk; k += 4) {
-            const double2 p = cmul(Vs[k * kCR + r], hs[k]);
+            const C p = cmul_t(Vs[k * kCR + r], hs[k]);
             a.x += p.x;
             a.y += p.y;
         }
@@ -105,12 +156,14 @@ __device__ __forceinline__ void tile_update(const double2* Vs, int nk, const dou
         a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
     }
     if (part == 0) {
-        double2 v = make_double2(0, 0);
+        C v;
+        v.x = 0;
+        v.y = 0;
         if (r < rows) {
-            v = w[r0 + r];
+            v = w64 ? from64<T>(w64[r0 + r]) : w[r0 + r];
             v.x -= a.x;
             v.y -= a.y;
-            if (hs) w[r0 + r] = v;
+            if (hs || w64) w[r0 + r] = v;
         }
         ws[r] = v;
     }
@@ -143,35 +196,42 @@ __device__ __forceinline__ void reduce_blocks(const double2* part, int nk, int n
     }
 }
 
-// out[0..nk) = V[:, 0..nk)^H w, after w -= V h_in when h_in is given.
-// Dynamic shared memory: nk kCR complex128.  part: nk x gridDim.x partials.
-__global__ void __launch_bounds__(kAT) cgs_kernel(long N, const double2* __restrict__ V, int nk, const double2* __restrict__ h_in,
-                                                  double2* __restrict__ w, double2* __restrict__ part, unsigned* ticket,
-                                                  double2* __restrict__ out)
+// out[0..nk) = V[:, 0..nk)^H w, after w -= V h_in when h_in is given (w read
+// from w64 when that is given).  Products and per-block sums in T, block
+// partials summed in FP64.  Dynamic shared memory: nk kCR entries of T's
+// complex type.  part: nk x gridDim.x partials.
+template <typename T>
+__global__ void __launch_bounds__(kAT) cgs_kernel(long N, const typename CT<T>::t* __restrict__ V, int nk, const double2* __restrict__ h_in,
+                                                  typename CT<T>::t* __restrict__ w, const double2* __restrict__ w64,
+                                                  double2* __restrict__ part, unsigned* ticket, double2* __restrict__ out)
 {
-    extern __shared__ double2 Vs[];
-    __shared__ double2 hs[kMaxM + 1];
-    __shared__ double2 ws[kCR];
+    using C = typename CT<T>::t;
+    extern __shared__ __align__(16) unsigned char cgs_smem[];
+    C* Vs = (C*)cgs_smem;
+    __shared__ C hs[kMaxM + 1];
+    __shared__ C ws[kCR];
     const long r0 = (long)blockIdx.x * kCR;
     const int rows = (int)min((long)kCR, N - r0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nrb = gridDim.x;
     if (h_in)
-        for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = h_in[k];
-    stage_tile(V, N, nk, r0, rows, Vs);
-    tile_update(Vs, nk, h_in ? hs : nullptr, w, r0, rows, ws);
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = from64<T>(h_in[k]);
+    stage_tile<T>(V, N, nk, r0, rows, Vs);
+    tile_update<T>(Vs, nk, h_in ? hs : nullptr, w, w64, r0, rows, ws);
     // column k by warp k % 8, lanes over the rows
     for (int k = warp; k < nk; k += kAT / 32) {
-        double2 p = make_double2(0, 0);
+        C p;
+        p.x = 0;
+        p.y = 0;
         for (int r = lane; r < kCR; r += 32) {
-            const double2 q = cconjmul(Vs[k * kCR + r], ws[r]);
-            p.x += r < rows ? q.x : 0.0;
-            p.y += r < rows ? q.y : 0.0;
+            const C q = cconjmul_t(Vs[k * kCR + r], ws[r]);
+            p.x += r < rows ? q.x : (T)0;
+            p.y += r < rows ? q.y : (T)0;
         }
         for (int o = 16; o > 0; o >>= 1) {
             p.x += __shfl_xor_sync(0xffffffffu, p.x, o);
             p.y += __shfl_xor_sync(0xffffffffu, p.y, o);
         }
-        if (lane == 0) part[(size_t)k * nrb + blockIdx.x] = p;
+        if (lane == 0) part[(size_t)k * nrb + blockIdx.x] = make_double2(p.x, p.y);
     }
     if (!last_block(ticket)) return;
     reduce_blocks(part, nk, nrb, out);
@@ -249,27 +309,33 @@ struct GivensArgs {
 
 // w -= V h_in (h_in may be null), then |w|^2 -> *wn2 (real part); with
 // gv.H, the last block also takes the Givens step of column gv.j.
-// Dynamic shared memory: nk kCR complex128.  part: gridDim.x partials.
-__global__ void __launch_bounds__(kAT) cgs_norm_kernel(long N, const double2* __restrict__ V, int nk, const double2* __restrict__ h_in,
-                                                       double2* __restrict__ w, double2* __restrict__ part, unsigned* ticket,
+// Dynamic shared memory: nk kCR entries.  part: gridDim.x partials.
+template <typename T>
+__global__ void __launch_bounds__(kAT) cgs_norm_kernel(long N, const typename CT<T>::t* __restrict__ V, int nk, const double2* __restrict__ h_in,
+                                                       typename CT<T>::t* __restrict__ w, double2* __restrict__ part, unsigned* ticket,
                                                        double2* __restrict__ wn2, GivensArgs gv)
 {
-    extern __shared__ double2 Vs[];
-    __shared__ double2 hs[kMaxM + 1];
-    __shared__ double2 ws[kCR];
+    using C = typename CT<T>::t;
+    extern __shared__ __align__(16) unsigned char cgs_smem[];
+    C* Vs = (C*)cgs_smem;
+    __shared__ C hs[kMaxM + 1];
+    __shared__ C ws[kCR];
+    __shared__ double red[kAT / 32];
     const long r0 = (long)blockIdx.x * kCR;
     const int rows = (int)min((long)kCR, N - r0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nrb = gridDim.x;
     if (h_in)
-        for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = h_in[k];
-    if (h_in) stage_tile(V, N, nk, r0, rows, Vs);
-    tile_update(Vs, h_in ? nk : 0, h_in ? hs : nullptr, w, r0, rows, ws);
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = from64<T>(h_in[k]);
+    if (h_in) stage_tile<T>(V, N, nk, r0, rows, Vs);
+    tile_update<T>(Vs, h_in ? nk : 0, h_in ? hs : nullptr, w, nullptr, r0, rows, ws);
     if (warp == 0) {
         double s2 = 0;
-        for (int r = lane; r < kCR; r += 32) s2 += ws[r].x * ws[r].x + ws[r].y * ws[r].y;
+        for (int r = lane; r < kCR; r += 32) s2 += (double)ws[r].x * ws[r].x + (double)ws[r].y * ws[r].y;
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        if (lane == 0) part[blockIdx.x] = make_double2(s2, 0.0);
+        if (lane == 0) red[0] = s2;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(red[0], 0.0);
     if (!last_block(ticket)) return;
     if (warp == 0) {
         double t = 0;
@@ -300,14 +366,20 @@ __global__ void __launch_bounds__(kThreads) add_zy_kernel(long N, const double2*
     x[i] = a;
 }
 
-// out = a / sqrt(re(*nrm2)) (0 when the norm is 0)
-__global__ void scale_inv_norm_kernel(long N, const double2* __restrict__ a, const double2* __restrict__ nrm2, double2* __restrict__ out)
+// out = a / sqrt(re(*nrm2)) (0 when the norm is 0), a read from a (T) or a64
+// (complex128); written to out (T) and, when given, out64 (complex128).
+template <typename T>
+__global__ void scale_inv_norm_kernel(long N, const typename CT<T>::t* __restrict__ a, const double2* __restrict__ a64,
+                                      const double2* __restrict__ nrm2, typename CT<T>::t* __restrict__ out, double2* __restrict__ out64)
 {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double n = sqrt(nrm2->x);
     const double s = n > 0 ? 1.0 / n : 0.0;
-    out[i] = make_double2(a[i].x * s, a[i].y * s);
+    const double2 v = a64 ? a64[i] : make_double2((double)a[i].x, (double)a[i].y);
+    const double2 o = make_double2(v.x * s, v.y * s);
+    out[i] = from64<T>(o);
+    if (out64) out64[i] = o;
 }
 
 __global__ void sub_kernel(long N, const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ out)
@@ -360,6 +432,8 @@ struct GmresWork {
     long N = 0;
     int m = 0, nrb = 0;
     double2 *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t = nullptr, *zin = nullptr;
+    float2 *V32 = nullptr, *w32 = nullptr;  // mixed precision: complex64 basis and work vector
+    double2* vcur = nullptr;                // mixed precision: the current basis vector in complex128
     double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double2 *h1 = nullptr, *h2 = nullptr, *part = nullptr, *sc = nullptr;  // sc: scalars (norms^2)
     double* res = nullptr;       // device: |g[j+1]| per step
@@ -368,8 +442,8 @@ struct GmresWork {
     cudaEvent_t ev[2] = {};
     void release()
     {
-        for (void* p : {(void*)V, (void*)Z, (void*)w, (void*)r, (void*)t, (void*)zin, (void*)H, (void*)cs, (void*)sn, (void*)g, (void*)y, (void*)h1,
-                        (void*)h2, (void*)part, (void*)sc, (void*)res, (void*)tickets})
+        for (void* p : {(void*)V, (void*)Z, (void*)w, (void*)r, (void*)t, (void*)zin, (void*)V32, (void*)w32, (void*)vcur, (void*)H, (void*)cs,
+                        (void*)sn, (void*)g, (void*)y, (void*)h1, (void*)h2, (void*)part, (void*)sc, (void*)res, (void*)tickets})
             cudaFree(p);
         if (res_host) cudaFreeHost(res_host);
         for (cudaEvent_t& e : ev)
@@ -411,6 +485,9 @@ GmresWork& workspace(OpsDev& d, long N, int m)
     dalloc(&W.r, sizeof(double2) * N);
     dalloc(&W.t, sizeof(double2) * N);
     dalloc(&W.zin, sizeof(double2) * N);
+    dalloc(&W.V32, sizeof(float2) * N * (m + 1));
+    dalloc(&W.w32, sizeof(float2) * N);
+    dalloc(&W.vcur, sizeof(double2) * N);
     dalloc(&W.H, sizeof(double2) * (m + 1) * m);
     dalloc(&W.cs, sizeof(double2) * m);
     dalloc(&W.sn, sizeof(double2) * m);
@@ -429,8 +506,10 @@ GmresWork& workspace(OpsDev& d, long N, int m)
     }
     for (cudaEvent_t& e : W.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     const int tile_max = (int)(sizeof(double2) * kCR * (kMaxM + 1));
-    CK(cudaFuncSetAttribute(cgs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max));
-    CK(cudaFuncSetAttribute(cgs_norm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max));
+    CK(cudaFuncSetAttribute(cgs_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max));
+    CK(cudaFuncSetAttribute(cgs_norm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max));
+    CK(cudaFuncSetAttribute(cgs_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max / 2));
+    CK(cudaFuncSetAttribute(cgs_norm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_max / 2));
     return W;
 }
 
@@ -438,7 +517,7 @@ GmresWork& workspace(OpsDev& d, long N, int m)
 void norm2(GmresWork& W, const double2* v, double2* out, cudaStream_t s)
 {
     GivensArgs none{};
-    cgs_norm_kernel<<<W.nrb, kAT, 0, s>>>(W.N, nullptr, 0, nullptr, (double2*)v, W.part, W.tickets + 3, out, none);
+    cgs_norm_kernel<double><<<W.nrb, kAT, 0, s>>>(W.N, nullptr, 0, nullptr, (double2*)v, W.part, W.tickets + 3, out, none);
 }
 
 }  // namespace
@@ -468,9 +547,15 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
         st.converged = 1;
         return DAFMM_OK;
     }
-    // one Arnoldi step: column j of V -> z_j, w = A z_j, orthogonalise, Givens
+    // Mixed precision keeps the inner cycles' basis in complex64 (CGS2 in FP32
+    // keeps it orthogonal to ~1e-7, far below the inner tolerance) and the
+    // current basis vector in complex128 for the preconditioner; FP64 cycles
+    // keep the complex128 basis.  The Hessenberg matrix, the rotations, the
+    // preconditioned basis Z and x stay FP64.
+    const bool lowp = o.precision == DAFMM_MIXED;
+    // one Arnoldi step: v_j -> z_j, w = A z_j, orthogonalise, Givens, v_{j+1}
     auto enqueue_step = [&](int j) {
-        double2* vj = W.V + (size_t)j * N;
+        const double2* vj = lowp ? W.vcur : W.V + (size_t)j * N;
         double2* zj = W.Z + (size_t)j * N;
         if (prec) {
             prec(M, (const double*)vj, (double*)zj, o.precision, s);
@@ -483,12 +568,22 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
         apply_matvec(t, d, 1, (const double*)W.zin, (double*)W.w, o.precision, s);
         st.matvecs++;
         // classical Gram-Schmidt, twice; then |w|, the Givens step and v_{j+1}
-        const size_t tile = sizeof(double2) * kCR * (size_t)(j + 1);
-        cgs_kernel<<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, nullptr, W.w, W.part, W.tickets + 0, W.h1);
-        cgs_kernel<<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, W.h1, W.w, W.part, W.tickets + 1, W.h2);
         GivensArgs gv{j, m, W.h1, W.h2, W.H, W.cs, W.sn, W.g, W.res};
-        cgs_norm_kernel<<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, W.h2, W.w, W.part, W.tickets + 2, W.sc + 2, gv);
-        scale_inv_norm_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.w, W.sc + 2, W.V + (size_t)(j + 1) * N);
+        if (lowp) {
+            const size_t tile = sizeof(float2) * kCR * (size_t)(j + 1);
+            cgs_kernel<float><<<W.nrb, kAT, tile, s>>>(N, W.V32, j + 1, nullptr, W.w32, W.w, W.part, W.tickets + 0, W.h1);
+            cgs_kernel<float><<<W.nrb, kAT, tile, s>>>(N, W.V32, j + 1, W.h1, W.w32, nullptr, W.part, W.tickets + 1, W.h2);
+            cgs_norm_kernel<float><<<W.nrb, kAT, tile, s>>>(N, W.V32, j + 1, W.h2, W.w32, W.part, W.tickets + 2, W.sc + 2, gv);
+            scale_inv_norm_kernel<float>
+                <<<blocks(N), kThreads, 0, s>>>(N, W.w32, nullptr, W.sc + 2, W.V32 + (size_t)(j + 1) * N, W.vcur);
+        } else {
+            const size_t tile = sizeof(double2) * kCR * (size_t)(j + 1);
+            cgs_kernel<double><<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, nullptr, W.w, nullptr, W.part, W.tickets + 0, W.h1);
+            cgs_kernel<double><<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, W.h1, W.w, nullptr, W.part, W.tickets + 1, W.h2);
+            cgs_norm_kernel<double><<<W.nrb, kAT, tile, s>>>(N, W.V, j + 1, W.h2, W.w, W.part, W.tickets + 2, W.sc + 2, gv);
+            scale_inv_norm_kernel<double>
+                <<<blocks(N), kThreads, 0, s>>>(N, W.w, nullptr, W.sc + 2, W.V + (size_t)(j + 1) * N, nullptr);
+        }
         CK(cudaMemcpyAsync(W.res_host + j, W.res, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaEventRecord(W.ev[j & 1], s));
     };
@@ -519,7 +614,10 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
         if (total >= o.max_iters) break;
         // one flexible GMRES cycle on A d = r, d0 = 0
         const double inner = o.precision == DAFMM_MIXED ? std::max(o.inner_tol, o.tol / rel * 0.5) : o.tol / rel * 0.5;
-        scale_inv_norm_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.r, W.sc + 1, W.V);
+        if (lowp)
+            scale_inv_norm_kernel<float><<<blocks(N), kThreads, 0, s>>>(N, nullptr, W.r, W.sc + 1, W.V32, W.vcur);
+        else
+            scale_inv_norm_kernel<double><<<blocks(N), kThreads, 0, s>>>(N, nullptr, W.r, W.sc + 1, W.V, nullptr);
         init_g_kernel<<<(m + 1 + 127) / 128, 128, 0, s>>>(m, W.sc + 1, W.g);
         const int steps = std::min(m, o.max_iters - total);  // steps this cycle may take
         enqueue_step(0);

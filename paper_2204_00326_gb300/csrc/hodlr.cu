@@ -90,7 +90,7 @@ constexpr int kHodlrMaxLevels = 24;  // levels of the apply launch
 
 struct HodlrDevLevel {
     int r = 0;
-    double2 *R64 = nullptr, *Ut64 = nullptr, *S64 = nullptr;
+    double2 *R64 = nullptr, *Ut64 = nullptr, *S64 = nullptr;  // float pairs (see to_pairs)
     float2 *R32 = nullptr, *Ut32 = nullptr, *S32 = nullptr;
 };
 
@@ -104,7 +104,7 @@ struct dafmm_hodlr {
     std::vector<dafmm::cd> leafInv;  // their inverses
     std::vector<dafmm::HodlrLevelHost> lv;
     // device
-    double2* inv64 = nullptr;
+    double2* inv64 = nullptr;  // float pairs (see to_pairs)
     float2* inv32 = nullptr;
     std::vector<dafmm::HodlrDevLevel> dlv;
     void* t_part = nullptr;  // partial sums of W x (complex128 size): rmax x N / leaf
@@ -191,10 +191,17 @@ void up(const std::vector<V>& h, V** d)
     CK(cudaMemcpy(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice));
 }
 
-std::vector<double2> to64(const std::vector<cd>& v)
+// complex128 factors as float pairs {re hi, im hi, re lo, im lo} in the 16
+// bytes of a double2 (hi the nearest float, lo the nearest float of the rest)
+std::vector<double2> to_pairs(const std::vector<cd>& v)
 {
     std::vector<double2> o(v.size());
-    for (size_t k = 0; k < v.size(); k++) o[k] = make_double2(v[k].real(), v[k].imag());
+    for (size_t k = 0; k < v.size(); k++) {
+        const double re = v[k].real(), im = v[k].imag();
+        const float rh = (float)re, ih = (float)im;
+        const float f[4] = {rh, ih, (float)(re - (double)rh), (float)(im - (double)ih)};
+        std::memcpy(&o[k], f, sizeof(f));
+    }
     return o;
 }
 std::vector<float2> to32(const std::vector<cd>& v)
@@ -311,37 +318,141 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <typename C>
-__device__ __forceinline__ void cmac(float& sr, float& si, C m, C v)
+// Arithmetic of the apply.  complex64 (mixed precision): float2 values, FP32
+// sums.  complex128: float pairs {re hi, im hi, re lo, im lo} in the 16 bytes
+// of a double2 (double-float arithmetic, about 48 significant bits: FP64
+// instructions issue at 1/64 of the FP32 rate on GB300), the factors stored
+// so, the input split and the result rounded to double once.
+__device__ __forceinline__ float4 as_f4(double2 d)
 {
-    sr = fmaf(m.x, v.x, fmaf(-m.y, v.y, sr));
-    si = fmaf(m.x, v.y, fmaf(m.y, v.x, si));
+    union {
+        double2 d;
+        float4 f;
+    } u;
+    u.d = d;
+    return u.f;
 }
-template <typename C>
-__device__ __forceinline__ void cmac(double& sr, double& si, C m, C v)
+__device__ __forceinline__ double2 as_d2(float4 f)
 {
-    sr = fma(m.x, v.x, fma(-m.y, v.y, sr));
-    si = fma(m.x, v.y, fma(m.y, v.x, si));
+    union {
+        double2 d;
+        float4 f;
+    } u;
+    u.f = f;
+    return u.d;
+}
+
+// (sh, sl) += a b for float pairs: the product's rounding error by FMA, the
+// cross terms, a two-sum into sh (explicitly rounded steps, never contracted).
+__device__ __forceinline__ void pf_mac(float& sh, float& sl, float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float t = __fadd_rn(sh, p);
+    const float v = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, v)), __fsub_rn(p, v));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// (h, l) = a + b for float pairs, renormalised.
+__device__ __forceinline__ void pf_add(float& h, float& l, float ah, float al, float bh, float bl)
+{
+    const float s = __fadd_rn(ah, bh);
+    const float v = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(ah, __fsub_rn(s, v)), __fsub_rn(bh, v)), __fadd_rn(al, bl));
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
 }
 
 template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+struct Ar;
 
-// Lane sums of four (re, im) accumulators, interleaved.
-template <typename T>
-__device__ __forceinline__ void warp_sum4(T (&re)[4], T (&im)[4])
-{
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            re[u] += __shfl_xor_sync(0xffffffffu, re[u], o);
-            im[u] += __shfl_xor_sync(0xffffffffu, im[u], o);
-        }
-}
+template <>
+struct Ar<float> {
+    using C = float2;
+    struct A {
+        float r, i;
+    };
+    static __device__ __forceinline__ A zero() { return A{0.f, 0.f}; }
+    static __device__ __forceinline__ void mac(A& a, C m, C v)
+    {
+        a.r = fmaf(m.x, v.x, fmaf(-m.y, v.y, a.r));
+        a.i = fmaf(m.x, v.y, fmaf(m.y, v.x, a.i));
+    }
+    static __device__ __forceinline__ void add(A& a, A b)
+    {
+        a.r += b.r;
+        a.i += b.i;
+    }
+    static __device__ __forceinline__ void add_c(A& a, C v)
+    {
+        a.r += v.x;
+        a.i += v.y;
+    }
+    static __device__ __forceinline__ A shfl_xor(A a, int o)
+    {
+        return A{__shfl_xor_sync(0xffffffffu, a.r, o), __shfl_xor_sync(0xffffffffu, a.i, o)};
+    }
+    static __device__ __forceinline__ C to_c(A a) { return make_float2(a.r, a.i); }
+    static __device__ __forceinline__ C sub(C x, A a) { return make_float2(x.x - a.r, x.y - a.i); }
+    static __device__ __forceinline__ C from64(double2 b) { return make_float2((float)b.x, (float)b.y); }
+    static __device__ __forceinline__ double2 to64(C x) { return make_double2(x.x, x.y); }
+};
+
+template <>
+struct Ar<double> {
+    using C = double2;  // holds a float pair
+    struct A {
+        float rh, rl, ih, il;
+    };
+    static __device__ __forceinline__ A zero() { return A{0.f, 0.f, 0.f, 0.f}; }
+    static __device__ __forceinline__ void mac(A& a, C mc, C vc)
+    {
+        const float4 m = as_f4(mc), v = as_f4(vc);
+        pf_mac(a.rh, a.rl, m.x, m.z, v.x, v.z);
+        pf_mac(a.rh, a.rl, -m.y, -m.w, v.y, v.w);
+        pf_mac(a.ih, a.il, m.x, m.z, v.y, v.w);
+        pf_mac(a.ih, a.il, m.y, m.w, v.x, v.z);
+    }
+    static __device__ __forceinline__ void add(A& a, A b)
+    {
+        pf_add(a.rh, a.rl, a.rh, a.rl, b.rh, b.rl);
+        pf_add(a.ih, a.il, a.ih, a.il, b.ih, b.il);
+    }
+    static __device__ __forceinline__ void add_c(A& a, C vc)
+    {
+        const float4 v = as_f4(vc);
+        pf_add(a.rh, a.rl, a.rh, a.rl, v.x, v.z);
+        pf_add(a.ih, a.il, a.ih, a.il, v.y, v.w);
+    }
+    static __device__ __forceinline__ A shfl_xor(A a, int o)
+    {
+        return A{__shfl_xor_sync(0xffffffffu, a.rh, o), __shfl_xor_sync(0xffffffffu, a.rl, o), __shfl_xor_sync(0xffffffffu, a.ih, o),
+                 __shfl_xor_sync(0xffffffffu, a.il, o)};
+    }
+    static __device__ __forceinline__ C to_c(A a) { return as_d2(make_float4(a.rh, a.ih, a.rl, a.il)); }
+    static __device__ __forceinline__ C sub(C xc, A a)
+    {
+        const float4 x = as_f4(xc);
+        float rh, rl, ih, il;
+        pf_add(rh, rl, x.x, x.z, -a.rh, -a.rl);
+        pf_add(ih, il, x.y, x.w, -a.ih, -a.il);
+        return as_d2(make_float4(rh, ih, rl, il));
+    }
+    static __device__ __forceinline__ C from64(double2 b)
+    {
+        const float rh = __double2float_rn(b.x), ih = __double2float_rn(b.y);
+        return as_d2(make_float4(rh, ih, __double2float_rn(b.x - (double)rh), __double2float_rn(b.y - (double)ih)));
+    }
+    static __device__ __forceinline__ double2 to64(C xc)
+    {
+        const float4 x = as_f4(xc);
+        return make_double2((double)x.x + (double)x.z, (double)x.y + (double)x.w);
+    }
+};
 
 // This CTA's columns [e0, e0 + E) of R and Ut of level l to L2.
 template <typename T>
@@ -357,9 +468,11 @@ __device__ __forceinline__ void prefetch_rows(const HArgs<T>& a, int l, long e0,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant__ HArgs<T> a)
+__global__ void __launch_bounds__(kHT, 1) hodlr_apply_kernel(const __grid_constant__ HArgs<T> a)
 {
     using C = typename C2<T>::t;
+    using P = Ar<T>;
+    using A = typename P::A;
     extern __shared__ __align__(16) unsigned char hsm[];
     C* sh = (C*)hsm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -382,23 +495,14 @@ __global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant_
     const long per = min(E, (long)max(lf, kHT));
     for (long g0 = e0; g0 < e0 + E; g0 += per) {
         __syncthreads();
-        for (long k = tid; k < per; k += kHT) {
-            const double2 v = a.b[g0 + k];
-            C c;
-            c.x = (T)v.x;
-            c.y = (T)v.y;
-            sh[k] = c;
-        }
+        for (long k = tid; k < per; k += kHT) sh[k] = P::from64(a.b[g0 + k]);
         __syncthreads();
         for (long k = tid; k < per; k += kHT) {
             const long li = k / lf * lf, i = k - li;
             const C* M = a.inv + (size_t)((g0 + li) / lf) * lf * lf + i;
-            T sr = 0, si = 0;
-            for (int j = 0; j < lf; j++) cmac(sr, si, M[(size_t)j * lf], sh[li + j]);
-            C o;
-            o.x = sr;
-            o.y = si;
-            a.x[g0 + k] = o;
+            A acc = P::zero();
+            for (int j = 0; j < lf; j++) P::mac(acc, M[(size_t)j * lf], sh[li + j]);
+            a.x[g0 + k] = P::to_c(acc);
         }
     }
     bool ok = true;
@@ -415,24 +519,19 @@ __global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant_
         // (four rows q of R per warp at a time, so that their loads overlap)
         for (long s0 = e0; s0 < e0 + E; s0 += m) {
             for (int q0 = warp; q0 < r; q0 += 4 * kW) {
-                T sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
+                A acc[4] = {P::zero(), P::zero(), P::zero(), P::zero()};
                 for (long i = s0 + lane; i < s0 + m; i += 32) {
                     const C xv = a.x[i];
 #pragma unroll
                     for (int u = 0; u < 4; u++)
-                        if (q0 + u * kW < r) cmac(sr[u], si[u], R[(size_t)(q0 + u * kW) * a.N + i], xv);
+                        if (q0 + u * kW < r) P::mac(acc[u], R[(size_t)(q0 + u * kW) * a.N + i], xv);
                 }
-                warp_sum4(sr, si);
-                if (lane < 4 && q0 + lane * kW < r) {
-                    C o;
+                for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                    for (int u = 0; u < 4; u++)
-                        if (u == lane) {
-                            o.x = sr[u];
-                            o.y = si[u];
-                        }
-                    a.part[(size_t)(q0 + lane * kW) * nslots + s0 / m] = o;
-                }
+                    for (int u = 0; u < 4; u++) P::add(acc[u], P::shfl_xor(acc[u], o));
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (lane == u && q0 + u * kW < r) a.part[(size_t)(q0 + u * kW) * nslots + s0 / m] = P::to_c(acc[u]);
             }
         }
         __syncthreads();  // this CTA's partials are written
@@ -453,23 +552,15 @@ __global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant_
             const int cols = (r + p - 1) / p;
             for (int pass = 0; pass < npass; pass++) {
                 const int aa = pass * rpp + tid / p;
-                T sr = 0, si = 0;
+                A acc = P::zero();
                 if (aa < R2) {
                     const C* row = Sn + (size_t)aa * R2;
                     const int b1 = min(r, (piece + 1) * cols);
 #pragma unroll 8
-                    for (int bb = piece * cols; bb < b1; bb++) cmac(sr, si, row[bb], sh[bb]);
+                    for (int bb = piece * cols; bb < b1; bb++) P::mac(acc, row[bb], sh[bb]);
                 }
-                for (int o = p / 2; o > 0; o >>= 1) {
-                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                    si += __shfl_xor_sync(0xffffffffu, si, o);
-                }
-                if (aa < R2 && piece == 0) {
-                    C o;
-                    o.x = sr;
-                    o.y = si;
-                    cb[(size_t)g * R2 + aa] = o;
-                }
+                for (int o = p / 2; o > 0; o >>= 1) P::add(acc, P::shfl_xor(acc, o));
+                if (aa < R2 && piece == 0) cb[(size_t)g * R2 + aa] = P::to_c(acc);
             }
             __syncthreads();
         }
@@ -501,68 +592,47 @@ __global__ void __launch_bounds__(kHT) hodlr_apply_kernel(const __grid_constant_
             __syncthreads();
             for (int pass = 0; pass < npass2; pass++) {
                 const int q = pass * rpp2 + tid / p2;
-                T sr = 0, si = 0;
+                A acc = P::zero();
                 if (q < r) {
-                    const C* P = cb + (size_t)ga * R2 + hoff + q;
+                    const C* Pq = cb + (size_t)ga * R2 + hoff + q;
 #pragma unroll 8
-                    for (long k = piece2; k < gn; k += p2) {
-                        const C v = __ldcg(P + (size_t)k * R2);
-                        sr += v.x;
-                        si += v.y;
-                    }
+                    for (long k = piece2; k < gn; k += p2) P::add_c(acc, __ldcg(Pq + (size_t)k * R2));
                 }
-                for (int o = p2 / 2; o > 0; o >>= 1) {
-                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                    si += __shfl_xor_sync(0xffffffffu, si, o);
-                }
-                if (q < r && piece2 == 0) {
-                    C o;
-                    o.x = sr;
-                    o.y = si;
-                    sh[q] = o;
-                }
+                for (int o = p2 / 2; o > 0; o >>= 1) P::add(acc, P::shfl_xor(acc, o));
+                if (q < r && piece2 == 0) sh[q] = P::to_c(acc);
             }
             __syncthreads();
             const int g = tid / (int)min(m, (long)kHT);
             for (long k = tid % min(m, (long)kHT); k < m; k += min(m, (long)kHT)) {
                 const long i = s0 + k;
-                T sr = 0, si = 0;
+                A acc = P::zero();
                 int q = g;
                 for (; q + 7 * tpe < r; q += 8 * tpe) {
                     C u[8];
 #pragma unroll
                     for (int v = 0; v < 8; v++) u[v] = U[(size_t)(q + v * tpe) * a.N + i];
 #pragma unroll
-                    for (int v = 0; v < 8; v++) cmac(sr, si, u[v], sh[q + v * tpe]);
+                    for (int v = 0; v < 8; v++) P::mac(acc, u[v], sh[q + v * tpe]);
                 }
-                for (; q < r; q += tpe) cmac(sr, si, U[(size_t)q * a.N + i], sh[q]);
-                if (tpe == 1) {
-                    C x = a.x[i];
-                    x.x -= sr;
-                    x.y -= si;
-                    a.x[i] = x;
-                } else {
-                    C o;
-                    o.x = sr;
-                    o.y = si;
-                    red[(size_t)g * m + k] = o;
-                }
+                for (; q < r; q += tpe) P::mac(acc, U[(size_t)q * a.N + i], sh[q]);
+                if (tpe == 1)
+                    a.x[i] = P::sub(a.x[i], acc);
+                else
+                    red[(size_t)g * m + k] = P::to_c(acc);
             }
             if (tpe > 1) {
                 __syncthreads();
                 for (long k = tid; k < m; k += kHT) {
-                    C x = a.x[s0 + k];
-                    for (int gg = 0; gg < tpe; gg++) {
-                        x.x -= red[(size_t)gg * m + k].x;
-                        x.y -= red[(size_t)gg * m + k].y;
-                    }
-                    a.x[s0 + k] = x;
+                    A acc = P::zero();
+                    for (int gg = 0; gg < tpe; gg++) P::add_c(acc, red[(size_t)gg * m + k]);
+                    a.x[s0 + k] = P::sub(a.x[s0 + k], acc);
                 }
             }
         }
     }
-    if (ok && sizeof(T) == 4)
-        for (long i = e0 + tid; i < e0 + E; i += kHT) a.xout[i] = make_double2(a.x[i].x, a.x[i].y);
+    // the result in complex128 (in place for complex128: each thread its own unknowns)
+    if (ok)
+        for (long i = e0 + tid; i < e0 + E; i += kHT) a.xout[i] = P::to64(a.x[i]);
     // the last CTA to leave re-arms the barrier for the next launch
     __syncthreads();
     if (tid == 0) {
@@ -805,7 +875,7 @@ dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf)
             for (int i = 0; i < lf; i++)
                 for (int j = 0; j < lf; j++)
                     invc[(size_t)b * lf * lf + (size_t)j * lf + i] = h->leafInv[(size_t)b * lf * lf + (size_t)i * lf + j];
-        up(to64(invc), &h->inv64);
+        up(to_pairs(invc), &h->inv64);
         up(to32(invc), &h->inv32);
         h->dlv.assign(H, HodlrDevLevel());
         for (int l = 0; l < H; l++) {
@@ -813,15 +883,15 @@ dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf)
             const HodlrLevelHost& L = h->lv[l];
             D.r = L.r;
             h->rmax = std::max(h->rmax, L.r);
-            up(to64(L.R), &D.R64);
+            up(to_pairs(L.R), &D.R64);
             up(to32(L.R), &D.R32);
             // Ut as r x N, so that the update reads it along the unknowns
             std::vector<cd> utt((size_t)L.r * N);
             for (long i = 0; i < N; i++)
                 for (int q = 0; q < L.r; q++) utt[(size_t)q * N + i] = L.Ut[(size_t)i * L.r + q];
-            up(to64(utt), &D.Ut64);
+            up(to_pairs(utt), &D.Ut64);
             up(to32(utt), &D.Ut32);
-            up(to64(L.Sinv), &D.S64);
+            up(to_pairs(L.Sinv), &D.S64);
             up(to32(L.Sinv), &D.S32);
         }
         const long nl = std::max<long>(N / h->leaf, 1);

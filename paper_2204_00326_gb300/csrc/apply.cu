@@ -1337,6 +1337,7 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
     static_assert(kLeafPerCta == 4, "a CTA takes one 2 x 2 quad of leaves (four consecutive Morton indices)");
     __shared__ __align__(16) C sn[9 * 256];
     __shared__ __align__(16) C vq[16][16];  // inputs of the 4 x 4 leaves around the quad, rounded to T once
+                                            // (complex128: split into float pairs, like sn)
     __shared__ C part[2][kLeafPerCta * 16];
     if (done != nullptr && blockIdx.x == 0 && threadIdx.x <= kMaxPass) done[threadIdx.x * kDoneStride] = 0;
     auto rnd = [](double2 d) {
@@ -1373,7 +1374,12 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
             C val;
             val.x = 0;
             val.y = 0;
-            if (src >= 0) val = rnd(v[(size_t)src * 16 + j]);
+            if (src >= 0) {
+                if constexpr (sizeof(T) == 8)
+                    val = df_split(v[(size_t)src * 16 + j]);  // float pairs, see below
+                else
+                    val = rnd(v[(size_t)src * 16 + j]);
+            }
             vq[pos][j] = val;
         }
         // 16-byte loads, several in flight per thread
@@ -1446,6 +1452,8 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
     __syncthreads();
     if (leaf < nleaf) {
         const int l = leaf - q0;
+        // complex128: the near blocks and inputs are float pairs, multiplied in double-float
+        float dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f}, eh[2] = {0.f, 0.f}, el[2] = {0.f, 0.f};
 #pragma unroll
         for (int sx = 0; sx < 3; sx++) {
             const int o = grp * 3 + sx;  // offset (sx - 1, grp - 1); outside the domain vq holds zeros
@@ -1453,9 +1461,18 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
             const C* B = sn + o * 256 + i;
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
-                cmac<T>(ar0, ai0, B[j * 16], vs[j]);
-                cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
+                if constexpr (sizeof(T) == 8) {
+                    df_cmac(dh[0], dl[0], eh[0], el[0], as_df(B[j * 16]), as_df(vs[j]));
+                    df_cmac(dh[1], dl[1], eh[1], el[1], as_df(B[(j + 1) * 16]), as_df(vs[j + 1]));
+                } else {
+                    cmac<T>(ar0, ai0, B[j * 16], vs[j]);
+                    cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
+                }
             }
+        }
+        if constexpr (sizeof(T) == 8) {
+            ar1 += ((double)dh[0] + (double)dl[0]) + ((double)dh[1] + (double)dl[1]);
+            ai1 += ((double)eh[0] + (double)el[0]) + ((double)eh[1] + (double)el[1]);
         }
     }
     C mine;
@@ -2137,7 +2154,7 @@ void run_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const double* 
     mark(prof, 1, s);
     mark(prof, 2, s);
     mark(prof, 3, s);
-    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
+    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.neardf : (const void*)d.near32);
     const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
     const bool comp = far && L - 1 >= t.top;
     const C* cm = comp ? (const C*)(sizeof(T) == 8 ? d.leafc.mdf : d.leafc.m32) : nullptr;
@@ -2318,15 +2335,19 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
     // near blocks, transposed to [o][j][i]
     std::vector<double2> n64(9 * 256);
     std::vector<float2> n32(9 * 256);
+    std::vector<float4> ndf(9 * 256);  // float pairs for the single-right-hand-side complex128 leaf kernel
     for (int o = 0; o < 9; o++)
         for (int i = 0; i < 16; i++)
             for (int j = 0; j < 16; j++) {
                 cd v = h.near[o * 256 + i * 16 + j];
                 n64[o * 256 + j * 16 + i] = make_double2(v.real(), v.imag());
                 n32[o * 256 + j * 16 + i] = make_float2((float)v.real(), (float)v.imag());
+                const float rh = (float)v.real(), ih = (float)v.imag();
+                ndf[o * 256 + j * 16 + i] = make_float4(rh, ih, (float)(v.real() - (double)rh), (float)(v.imag() - (double)ih));
             }
     upload_vec(n64, &d.near64);
     upload_vec(n32, &d.near32);
+    upload_vec(ndf, &d.neardf);
     // near-neighbour table of the leaves
     const int nleaf = t.nb * t.nb;
     std::vector<int> nbr((size_t)nleaf * 9, -1);
@@ -2444,6 +2465,7 @@ void free_ops(OpsDev& d)
     free_group(d.m2l);
     d.lv.clear();
     cudaFree(d.near64);
+    cudaFree(d.neardf);
     cudaFree(d.near32);
     cudaFree(d.nbr);
     cudaFree(d.q);

@@ -107,6 +107,7 @@ struct OpsDev {
     Fused fz;                   // single right-hand side: every pass in one launch
     BsrDev leafc;               // rows leaves: the L2L from level L-1 composed with L2P (16 x R per block)
     double2* near64 = nullptr;  // 9 x 16 x 16, source offset (sx,sy) -> (sy+1)*3+(sx+1)
+    float4* neardf = nullptr;   // the same as float pairs {re hi, im hi, re lo, im lo}
     float2* near32 = nullptr;
     int* nbr = nullptr;         // [nleaf][9] source leaf of each near offset, -1 outside
     double* q = nullptr;        // contrast at the N nodes

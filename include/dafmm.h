@@ -51,7 +51,12 @@ extern "C" {
 #define DAFMM_ECUDA 6       /* CUDA runtime error or no device */
 
 /* Arithmetic of an operator application. */
-#define DAFMM_FP64 0        /* complex128 operators and vectors, FP64 math */
+#define DAFMM_FP64 0        /* complex128 operators and vectors.  One right-hand
+                               side (dafmm_matvec, hodlr_solve) computes in
+                               double-float (float pairs, unit roundoff 2^-48:
+                               FP64 issues at 1/64 of the FP32 rate on GB300)
+                               and rounds results to double; several
+                               right-hand sides compute in FP64 */
 #define DAFMM_MIXED 1       /* complex64 operators and coefficients, FP32 math;
                                boundary vectors stay complex128 */
 
@@ -227,11 +232,14 @@ int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v_dev, double* ou
  * (the Hybrid solver, Eq. hybrid; right rather than left preconditioning so
  * that GMRES minimises the unpreconditioned residual the paper's stopping
  * rule measures).  Every outer step forms the true residual f - A x with the
- * FP64 DAFMM; inner cycles apply A (and M) in opts->precision.  Arnoldi,
- * Hessenberg, Givens rotations and vector updates are FP64 on the device.
- * f_dev: N complex128 (not modified); x_dev: N complex128, in: initial guess,
- * out: solution.  Allocates its Krylov workspace (N x (2m+1) complex128) for
- * the duration of the call and synchronises the stream.
+ * FP64 DAFMM; inner cycles apply A (and M) in opts->precision.  The
+ * Hessenberg matrix, Givens rotations, preconditioned basis and x are FP64
+ * on the device; the Arnoldi basis is complex128 in FP64 cycles and
+ * complex64 in the inner cycles of DAFMM_MIXED.  A zero initial guess takes
+ * r = f without an application.  f_dev: N complex128 (not modified); x_dev:
+ * N complex128, in: initial guess, out: solution.  Its Krylov workspace is
+ * kept on the ops handle between calls (grown when N or m grows); calls on
+ * one handle must be ordered.  Synchronises the stream.
  * Returns DAFMM_OK when converged, DAFMM_ENOTCONV when max_iters was reached
  * (x holds the last iterate, st the residual), DAFMM_EBADARG, DAFMM_ENOMEM,
  * DAFMM_ECUDA.
@@ -264,8 +272,9 @@ int hodlr_factor(const dafmm_ops* ops, int rank, double tol, int leaf_size, dafm
  * per level; each barrier wait has a limit (about 0.2 s), after which the
  * launch sets the handle's error flag and returns (see hodlr_sync).
  * b_dev, x_dev: N complex128 on the device; x_dev == b_dev is allowed.
- * precision: DAFMM_FP64, or DAFMM_MIXED (complex64 factors and arithmetic,
- * complex128 boundary vectors).  Asynchronous on stream.  Calls on one
+ * precision: DAFMM_FP64 (factors as float pairs, double-float arithmetic,
+ * result rounded to double), or DAFMM_MIXED (complex64 factors and
+ * arithmetic); boundary vectors are complex128.  Asynchronous on stream.  Calls on one
  * handle must be ordered (one stream): they share work buffers.
  */
 int hodlr_solve(const dafmm_hodlr* M, int nrhs, const double* b_dev, double* x_dev, int precision, void* stream);

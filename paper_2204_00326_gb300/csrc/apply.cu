@@ -1109,30 +1109,41 @@ __device__ __forceinline__ void batch_rows_h(float (&ar)[MR], float (&ai)[MR], c
     }
 }
 
+// Complex128 (float pairs, double-float arithmetic as in Acc<double>):
+// acc[m] += M[m][k] x[k] with (hi, lo) accumulators per row.
 template <int H, int MR>
-__device__ __forceinline__ void batch_rows_h(double (&ar)[MR], double (&ai)[MR], const double2* M, const double2* xs, int ncol, int ld, int xst)
+__device__ __forceinline__ void batch_rows_df_h(float (&rh)[MR], float (&rl)[MR], float (&ih)[MR], float (&il)[MR], const double2* M,
+                                                const double2* xs, int ncol, int ld, int xst)
 {
     for (int k = 0; k < ncol; k++) {
-        const double2 x = xs[k * xst];
+        const float4 x = as_df(xs[k * xst]);
 #pragma unroll
-        for (int m = 0; m < H; m++) {
-            const double2 q = M[k * ld + m];
-            ar[m] = fma(q.x, x.x, fma(-q.y, x.y, ar[m]));
-            ai[m] = fma(q.x, x.y, fma(q.y, x.x, ai[m]));
-        }
+        for (int m = 0; m < H; m++) df_cmac(rh[m], rl[m], ih[m], il[m], as_df(M[k * ld + m]), x);
+    }
+}
+
+template <int MR, int H = 2>
+__device__ __forceinline__ void batch_rows_df(int h, float (&rh)[MR], float (&rl)[MR], float (&ih)[MR], float (&il)[MR], const double2* M,
+                                              const double2* xs, int ncol, int ld, int xst)
+{
+    if constexpr (H <= MR) {
+        if (h == H)
+            batch_rows_df_h<H, MR>(rh, rl, ih, il, M, xs, ncol, ld, xst);
+        else
+            batch_rows_df<MR, H + 2>(h, rh, rl, ih, il, M, xs, ncol, ld, xst);
     }
 }
 
 // Dispatch on the lane's row count h (even, at most MR; uniform over the CTA).
-template <typename T, int MR, int H = 2>
-__device__ __forceinline__ void batch_rows(int h, T (&ar)[MR], T (&ai)[MR], const typename V2<T>::t* M, const typename V2<T>::t* xs, int ncol,
-                                           int ld, int xst)
+template <int MR, int H = 2>
+__device__ __forceinline__ void batch_rows(int h, float (&ar)[MR], float (&ai)[MR], const float2* M, const float2* xs, int ncol, int ld,
+                                           int xst)
 {
     if constexpr (H <= MR) {
         if (h == H)
             batch_rows_h<H, MR>(ar, ai, M, xs, ncol, ld, xst);
         else
-            batch_rows<T, MR, H + 2>(h, ar, ai, M, xs, ncol, ld, xst);
+            batch_rows<MR, H + 2>(h, ar, ai, M, xs, ncol, ld, xst);
     }
 }
 
@@ -1163,9 +1174,10 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
     }
     __syncthreads();
     for (int k = 0; k < 2 && cb + k < ce; k++) batch_issue<T>(g, recs, cb + k, stage_raw(k), &bar[k], nrhs, nrhs_pad, bulk_x, tid, blockDim.x);
-    T ar[MR], ai[MR];
+    // complex64: FP32 accumulators; complex128: float pairs (double-float)
+    float ar[MR], ai[MR], al[MR], bl[MR];
 #pragma unroll
-    for (int m = 0; m < MR; m++) ar[m] = ai[m] = 0;
+    for (int m = 0; m < MR; m++) ar[m] = ai[m] = al[m] = bl[m] = 0.f;
     int pslot = cb;
     for (int c = cb, it = 0; c < ce; c++, it++) {
         const int s = it & 1;
@@ -1196,7 +1208,12 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
         // rows of this lane: [gsel h, gsel h + h), h even
         const int h = ((ro + 3) >> 2) << 1;
         const int i0 = gsel * h;
-        if (r < nrhs) batch_rows<T, MR>(h, ar, ai, stage(s) + i0, xs + r, ncol, ld, nrhs_pad);
+        if (r < nrhs) {
+            if constexpr (sizeof(T) == 8)
+                batch_rows_df<MR>(h, ar, al, ai, bl, stage(s) + i0, xs + r, ncol, ld, nrhs_pad);
+            else
+                batch_rows<MR>(h, ar, ai, stage(s) + i0, xs + r, ncol, ld, nrhs_pad);
+        }
         __syncthreads();  // everyone is done with this stage (matrix and inputs)
         if (c + 2 < ce) batch_issue<T>(g, recs, c + 2, stage_raw(s), &bar[s], nrhs, nrhs_pad, bulk_x, tid, blockDim.x);
         const bool row_ends = (c + 1 == ce) || recs[2 * (c + 1)].x != ra.x || recs[2 * (c + 1)].y != ra.y;
@@ -1213,18 +1230,24 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
                     const int i = i0 + m;
                     if (i < ro && m < h) {
                         C* q = dst + (size_t)i * nrhs + r;
-                        T re = ar[m], im = ai[m];
-                        if (whole && add) {
-                            const C o = *q;
-                            re += o.x;
-                            im += o.y;
+                        if constexpr (sizeof(T) == 8) {
+                            float4 o = make_float4(ar[m], ai[m], al[m], bl[m]);
+                            if (whole && add) o = df4_add(o, as_df(*q));
+                            *q = df_bits(o);
+                        } else {
+                            T re = ar[m], im = ai[m];
+                            if (whole && add) {
+                                const C o = *q;
+                                re += o.x;
+                                im += o.y;
+                            }
+                            C o;
+                            o.x = re;
+                            o.y = im;
+                            *q = o;
                         }
-                        C o;
-                        o.x = re;
-                        o.y = im;
-                        *q = o;
                     }
-                    ar[m] = ai[m] = 0;
+                    ar[m] = ai[m] = al[m] = bl[m] = 0.f;
                 }
             }
             if (!whole) {
@@ -1237,21 +1260,28 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
                 if (s_last) {
                     __threadfence();
                     for (int qq = tid; qq < ro * nrhs; qq += blockDim.x) {
-                        T sr = 0, si = 0;
-                        if (add) {
-                            const C o = yrow[qq];
-                            sr = o.x;
-                            si = o.y;
+                        if constexpr (sizeof(T) == 8) {
+                            float4 acc = add ? as_df(yrow[qq]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            for (int cc = c0; cc < c1; cc = (cc / kpc + 1) * kpc)
+                                acc = df4_add(acc, as_df(__ldcg(&P[(size_t)cc * Pld * nrhs + qq])));
+                            yrow[qq] = df_bits(acc);
+                        } else {
+                            T sr = 0, si = 0;
+                            if (add) {
+                                const C o = yrow[qq];
+                                sr = o.x;
+                                si = o.y;
+                            }
+                            for (int cc = c0; cc < c1; cc = (cc / kpc + 1) * kpc) {
+                                const C p = __ldcg(&P[(size_t)cc * Pld * nrhs + qq]);
+                                sr += p.x;
+                                si += p.y;
+                            }
+                            C o;
+                            o.x = sr;
+                            o.y = si;
+                            yrow[qq] = o;
                         }
-                        for (int cc = c0; cc < c1; cc = (cc / kpc + 1) * kpc) {
-                            const C p = __ldcg(&P[(size_t)cc * Pld * nrhs + qq]);
-                            sr += p.x;
-                            si += p.y;
-                        }
-                        C o;
-                        o.x = sr;
-                        o.y = si;
-                        yrow[qq] = o;
                     }
                     if (tid == 0) cnt[c0] = 0;
                 }
@@ -1278,20 +1308,36 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
     for (int t = threadIdx.x; t < 16 * nrhs; t += blockDim.x) {
         const int i = t / nrhs, r = t - i * nrhs;
         T ar = 0, ai = 0;
+        // complex128: near blocks, inputs, L2P and locals are float pairs (double-float)
+        float dh = 0.f, dl = 0.f, eh = 0.f, el = 0.f;
         for (int o = 0; o < 9; o++) {
             const int src = nbr[leaf * 9 + o];
             if (src < 0) continue;
             const C* vs = vin + (size_t)src * 16 * nrhs + r;
             const C* B = sn + o * 256 + i;
 #pragma unroll
-            for (int j = 0; j < 16; j++) cmac<T>(ar, ai, B[j * 16], vs[(size_t)j * nrhs]);
+            for (int j = 0; j < 16; j++) {
+                if constexpr (sizeof(T) == 8)
+                    df_cmac(dh, dl, eh, el, as_df(B[j * 16]), as_df(vs[(size_t)j * nrhs]));
+                else
+                    cmac<T>(ar, ai, B[j * 16], vs[(size_t)j * nrhs]);
+            }
         }
         if (l2p_rowptr != nullptr && l2p_rowptr[leaf + 1] > l2p_rowptr[leaf]) {
             const int e = l2p_rowptr[leaf];
             const C* U = l2p + l2p_moff[e] + i;
             const C* u = lc + (size_t)leaf * ldl * nrhs + r;
             const int ri = l2p_rin[e];
-            for (int j = 0; j < ri; j++) cmac<T>(ar, ai, U[j * 16], u[(size_t)j * nrhs]);
+            for (int j = 0; j < ri; j++) {
+                if constexpr (sizeof(T) == 8)
+                    df_cmac(dh, dl, eh, el, as_df(U[j * 16]), as_df(u[(size_t)j * nrhs]));
+                else
+                    cmac<T>(ar, ai, U[j * 16], u[(size_t)j * nrhs]);
+            }
+        }
+        if constexpr (sizeof(T) == 8) {
+            ar = (double)dh + (double)dl;
+            ai = (double)eh + (double)el;
         }
         const size_t gi = ((size_t)leaf * 16 + i) * nrhs + r;
         const double2 vv = v[gi];
@@ -1493,6 +1539,13 @@ __global__ void to_c64_kernel(long n, const double2* __restrict__ a, float2* __r
 {
     long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (k < n) b[k] = make_float2((float)a[k].x, (float)a[k].y);
+}
+
+// complex128 as float pairs {re hi, im hi, re lo, im lo}
+__global__ void to_df_kernel(long n, const double2* __restrict__ a, double2* __restrict__ b)
+{
+    long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (k < n) b[k] = df_split(a[k]);
 }
 
 #define CK(x)                                                                                     \
@@ -1999,7 +2052,7 @@ PassArgs<T> pass_args(const Tree& t, const OpsDev& d, const Bufs<T>& b, const ty
     a.rbase = g.rbase[p];
     a.cbase = g.cbase[p];
     a.xmap = g.xmap[p];
-    a.mats = (const C*)(sizeof(T) == 8 ? bs.m64 : bs.m32);
+    a.mats = (const C*)(sizeof(T) == 8 ? bs.mdf : bs.m32);  // complex128: float pairs
     if (pr.kind == 0) {
         a.x = nu == t.L ? vin : b.mp[nu + 1];
         a.y = b.mp[nu];
@@ -2228,12 +2281,14 @@ void run_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, 
     const int nleaf = t.nb * t.nb;
     mark(prof, 0, s);
     const C* vin;
+    const long nv = N * nrhs;
     if (sizeof(T) == 4) {
-        const long n = N * nrhs;
-        to_c64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (const double2*)v, v32);
+        to_c64_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, (const double2*)v, v32);
         vin = (const C*)v32;
     } else {
-        vin = (const C*)v;
+        // complex128: every pass and the leaf kernel compute in double-float (see Acc<double>)
+        to_df_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, (const double2*)v, (double2*)d.vdf);
+        vin = (const C*)d.vdf;
     }
     const bool far = t.top <= L;
     if (far)
@@ -2244,11 +2299,11 @@ void run_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, 
     if (far)
         for (int nu = t.top; nu < L; nu++) launch_group_batched<T>(t, d, b, vin, d.down[nu], nrhs, s);
     mark(prof, 3, s);
-    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.near64 : (const void*)d.near32);
+    const C* nearp = (const C*)(sizeof(T) == 8 ? (const void*)d.neardf : (const void*)d.near32);
     const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
     leaf_batched_kernel<T><<<(unsigned)nleaf, 256, 0, s>>>(
         nleaf, nrhs, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
-        l2p ? (const C*)(sizeof(T) == 8 ? l2p->m64 : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
+        l2p ? (const C*)(sizeof(T) == 8 ? l2p->mdf : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
         (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
     CK(cudaGetLastError());
     mark(prof, 4, s);
@@ -2391,6 +2446,9 @@ void ensure_scratch(const Tree& t, OpsDev& d, int nrhs)
     cudaFree(d.v32);
     d.v32 = nullptr;
     dev_alloc(&d.v32, sizeof(float2) * (size_t)t.N * nrhs);
+    cudaFree(d.vdf);
+    d.vdf = nullptr;
+    dev_alloc(&d.vdf, sizeof(float4) * (size_t)t.N * nrhs);
     cudaFree(d.part);
     d.part = nullptr;
     dev_alloc((double2**)&d.part, sizeof(double2) * std::max<size_t>(d.part_elems, 1) * nrhs);
@@ -2470,6 +2528,7 @@ void free_ops(OpsDev& d)
     cudaFree(d.nbr);
     cudaFree(d.q);
     cudaFree(d.v32);
+    cudaFree(d.vdf);
     cudaFree(d.part);
     cudaFree(d.err);
     d = OpsDev();

@@ -112,6 +112,7 @@ struct OpsDev {
     int* nbr = nullptr;         // [nleaf][9] source leaf of each near offset, -1 outside
     double* q = nullptr;        // contrast at the N nodes
     float2* v32 = nullptr;      // complex64 copy of the input (mixed precision)
+    float4* vdf = nullptr;      // float-pair copy of the input (several right-hand sides, complex128)
     void* part = nullptr;       // chunk partials of the largest group (complex128 size)
     size_t part_elems = 0;      // complex elements per right-hand side in part
     int nrhs_cap = 0;           // scratch sized for this many right-hand sides

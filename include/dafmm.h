@@ -51,12 +51,11 @@ extern "C" {
 #define DAFMM_ECUDA 6       /* CUDA runtime error or no device */
 
 /* Arithmetic of an operator application. */
-#define DAFMM_FP64 0        /* complex128 operators and vectors.  One right-hand
-                               side (dafmm_matvec, hodlr_solve) computes in
+#define DAFMM_FP64 0        /* complex128 operators and vectors, computed in
                                double-float (float pairs, unit roundoff 2^-48:
                                FP64 issues at 1/64 of the FP32 rate on GB300)
-                               and rounds results to double; several
-                               right-hand sides compute in FP64 */
+                               with results rounded to double; the epilogue
+                               v + kappa^2 q (K v) is FP64 */
 #define DAFMM_MIXED 1       /* complex64 operators and coefficients, FP32 math;
                                boundary vectors stay complex128 */
 

@@ -4,9 +4,10 @@ Tolerances: FP64 mode 1e-10 relative 2-norm against the oracle's operator A
 (the DAFMM is an approximation of A to about eps_nca = 1e-12 per block, and
 the two quadratures agree to ~1e-13).  The single-right-hand-side FP64
 launch computes in double-float (float pairs, unit roundoff u = 2^-48 =
-3.6e-15); with the same |U| |V| ~ 1e2 amplification as below, its rounding
-(seen in the linearity defect and against the native complex128 batched
-path) stays under ~1e-12, checked at DF_TOL = 1e-11.  Mixed mode (complex64 operators and
+3.6e-15), and so does the several-right-hand-side path; with the same
+|U| |V| ~ 1e2 amplification as below, the rounding (seen in the linearity
+defect and between the two paths) stays under ~1e-12, checked at
+DF_TOL = 1e-11.  Mixed mode (complex64 operators and
 FP32 accumulation) is checked at 2e-5: complex64 rounds each stored operator
 entry to 6e-8 relative, and the realised NCA factors amplify that by the
 norms of the interpolation operators (|U|, |V| up to ~1e2), giving a few 1e-6
@@ -204,9 +205,8 @@ def test_batched_matvec_matches_single(N, op128, nrhs):
     """Several right-hand sides in one application equal one-at-a-time applications."""
     w = W.GRID128_K40
     V = torch.as_tensor(W.random_vector(w.N, nrhs, seed=60 + nrhs), device="cuda").contiguous()
-    # FP32 sums grouped differently in the two paths: compare at the mixed
-    # tolerance; FP64 several at once is native complex128, one at a time
-    # double-float: compare at the double-float rounding bound
+    # sums grouped differently in the two paths: compare at the mixed
+    # tolerance, and at the double-float rounding bound in FP64
     for prec, tol in ((N.DAFMM_FP64, DF_TOL), (N.DAFMM_MIXED, MIXED_TOL)):
         Y = op128.matvec(V, precision=prec)
         for k in sorted({0, nrhs // 2, nrhs - 1}):

@@ -145,8 +145,16 @@ typedef struct gmres_opts {
     double* history;    /* optional host array: relative residuals (true residual at
                            each restart, least-squares estimate in between) */
     int history_len;    /* its length */
-    int reserved[6];    /* must be zero */
+    int side;           /* side of the preconditioner M: DAFMM_PREC_RIGHT (0,
+                           default; GMRES minimises the residual the stopping
+                           rule measures) or DAFMM_PREC_LEFT (1; the paper's
+                           M^{-1} A x = M^{-1} f, Eq. hybrid, with the same
+                           FP64 true-residual stopping rule at every restart) */
+    int reserved[5];    /* must be zero */
 } gmres_opts;
+
+#define DAFMM_PREC_RIGHT 0
+#define DAFMM_PREC_LEFT 1
 
 /* What gmres_solve did. */
 typedef struct gmres_stats {

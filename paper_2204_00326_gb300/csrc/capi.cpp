@@ -278,6 +278,7 @@ void check_gmres(const dafmm_ops* ops, const double* f, const double* x, const g
         fail(DAFMM_EBADARG, "inner_tol must lie in (0, 1) in mixed precision");
     for (int v : opts->reserved)
         if (v) fail(DAFMM_EBADARG, "reserved options must be zero");
+    if (opts->side != DAFMM_PREC_RIGHT && opts->side != DAFMM_PREC_LEFT) fail(DAFMM_EBADARG, "side must be DAFMM_PREC_RIGHT or DAFMM_PREC_LEFT");
     if (f == x) fail(DAFMM_EBADARG, "f and x must not overlap");
 }
 
@@ -561,6 +562,8 @@ int gmres_solve_learned(dafmm_ops* ops, const dafmm_hodlr* M, dafmm_unet* net, i
         check_gmres(ops, f, x, opts, st);
         if (!net || !ls) fail(DAFMM_EBADARG, "NULL argument");
         if (flags & ~3) fail(DAFMM_EBADARG, "unknown flags");
+        if ((flags & 2) && opts->side == DAFMM_PREC_LEFT)
+            fail(DAFMM_EBADARG, "the coarse correction is a right preconditioner (side must be DAFMM_PREC_RIGHT)");
         if (M && hodlr_tree(M) != ops->tree) fail(DAFMM_EBADARG, "the preconditioner was built on another tree");
         const Tree& t = ops->tree->t;
         cudaStream_t s = (cudaStream_t)stream;

@@ -51,10 +51,6 @@ constexpr int kMaxM = 128;
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ double2 cconjmul(double2 a, double2 b)  // conj(a) * b
-{
-    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
 
 // True in the last block of the grid to get here (its partials and everyone
 // else's are visible to it); that block re-arms the ticket.
@@ -347,9 +343,10 @@ __global__ void __launch_bounds__(kAT) cgs_norm_kernel(long N, const typename CT
     }
 }
 
-// x[i] += sum_{k<nk} Z[i, k] y[k]
-__global__ void __launch_bounds__(kThreads) add_zy_kernel(long N, const double2* __restrict__ Z, long ldz, int nk,
-                                                          const double2* __restrict__ y, double2* __restrict__ x)
+// x[i] += sum_{k<nk} Z[i, k] y[k]  (Z complex128 or complex64)
+template <typename C>
+__global__ void __launch_bounds__(kThreads) add_zy_kernel(long N, const C* __restrict__ Z, long ldz, int nk, const double2* __restrict__ y,
+                                                          double2* __restrict__ x)
 {
     __shared__ double2 ys[kMaxM];
     for (int k = threadIdx.x; k < nk; k += blockDim.x) ys[k] = y[k];
@@ -359,7 +356,8 @@ __global__ void __launch_bounds__(kThreads) add_zy_kernel(long N, const double2*
     double2 a = x[i];
 #pragma unroll 8
     for (int k = 0; k < nk; k++) {
-        const double2 p = cmul(Z[(size_t)k * ldz + i], ys[k]);
+        const C z = Z[(size_t)k * ldz + i];
+        const double2 p = cmul(make_double2((double)z.x, (double)z.y), ys[k]);
         a.x += p.x;
         a.y += p.y;
     }
@@ -554,19 +552,30 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
     // preconditioned basis Z and x stay FP64.
     const bool lowp = o.precision == DAFMM_MIXED;
     // one Arnoldi step: v_j -> z_j, w = A z_j, orthogonalise, Givens, v_{j+1}
+    // left preconditioning (the paper's M^{-1} A x = M^{-1} f): w = M^{-1} A v_j and
+    // x += V y; right preconditioning: z_j = M^{-1} v_j, w = A z_j and x += Z y
+    const bool left = prec && o.side == DAFMM_PREC_LEFT;
     auto enqueue_step = [&](int j) {
         const double2* vj = lowp ? W.vcur : W.V + (size_t)j * N;
-        double2* zj = W.Z + (size_t)j * N;
-        if (prec) {
-            prec(M, (const double*)vj, (double*)zj, o.precision, s);
+        if (left) {
+            CK(cudaMemcpyAsync(W.zin, vj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+            apply_matvec(t, d, 1, (const double*)W.zin, (double*)W.t, o.precision, s);
+            st.matvecs++;
+            prec(M, (const double*)W.t, (double*)W.w, o.precision, s);
             st.precond_applies++;
         } else {
-            CK(cudaMemcpyAsync(zj, vj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+            double2* zj = W.Z + (size_t)j * N;
+            if (prec) {
+                prec(M, (const double*)vj, (double*)zj, o.precision, s);
+                st.precond_applies++;
+            } else {
+                CK(cudaMemcpyAsync(zj, vj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+            }
+            // fixed buffers keep the captured application valid from one step to the next
+            CK(cudaMemcpyAsync(W.zin, zj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+            apply_matvec(t, d, 1, (const double*)W.zin, (double*)W.w, o.precision, s);
+            st.matvecs++;
         }
-        // fixed buffers keep the captured application valid from one step to the next
-        CK(cudaMemcpyAsync(W.zin, zj, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
-        apply_matvec(t, d, 1, (const double*)W.zin, (double*)W.w, o.precision, s);
-        st.matvecs++;
         // classical Gram-Schmidt, twice; then |w|, the Givens step and v_{j+1}
         GivensArgs gv{j, m, W.h1, W.h2, W.H, W.cs, W.sn, W.g, W.res};
         if (lowp) {
@@ -612,13 +621,24 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
             break;
         }
         if (total >= o.max_iters) break;
-        // one flexible GMRES cycle on A d = r, d0 = 0
+        // one flexible GMRES cycle on A d = r (left: M^{-1} A d = M^{-1} r), d0 = 0
         const double inner = o.precision == DAFMM_MIXED ? std::max(o.inner_tol, o.tol / rel * 0.5) : o.tol / rel * 0.5;
+        const double2* r0 = W.r;
+        double2* r0n2 = W.sc + 1;
+        double rn0 = rn;  // norm of the cycle's starting vector
+        if (left) {
+            prec(M, (const double*)W.r, (double*)W.t, o.precision, s);
+            st.precond_applies++;
+            norm2(W, W.t, W.sc + 3, s);
+            rn0 = read_sqrt(W.sc + 3);
+            r0 = W.t;
+            r0n2 = W.sc + 3;
+        }
         if (lowp)
-            scale_inv_norm_kernel<float><<<blocks(N), kThreads, 0, s>>>(N, nullptr, W.r, W.sc + 1, W.V32, W.vcur);
+            scale_inv_norm_kernel<float><<<blocks(N), kThreads, 0, s>>>(N, nullptr, r0, r0n2, W.V32, W.vcur);
         else
-            scale_inv_norm_kernel<double><<<blocks(N), kThreads, 0, s>>>(N, nullptr, W.r, W.sc + 1, W.V, nullptr);
-        init_g_kernel<<<(m + 1 + 127) / 128, 128, 0, s>>>(m, W.sc + 1, W.g);
+            scale_inv_norm_kernel<double><<<blocks(N), kThreads, 0, s>>>(N, nullptr, r0, r0n2, W.V, nullptr);
+        init_g_kernel<<<(m + 1 + 127) / 128, 128, 0, s>>>(m, r0n2, W.g);
         const int steps = std::min(m, o.max_iters - total);  // steps this cycle may take
         enqueue_step(0);
         int queued = 1, j = 0;
@@ -636,7 +656,7 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
             }
             CK(cudaEventSynchronize(W.ev[j & 1]));
             total++;
-            const double est = W.res_host[j] / rn;
+            const double est = W.res_host[j] / rn0;
             if (o.history && total < o.history_len) o.history[total] = est * rel;
             if (est <= inner || j + 1 >= steps) {
                 j++;
@@ -650,7 +670,12 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
             e1 = est;
         }
         backsolve_kernel<<<1, kMaxM, 0, s>>>(j, m, W.H, W.g, W.y);
-        add_zy_kernel<<<blocks(N), kThreads, 0, s>>>(N, W.Z, N, j, W.y, X);
+        if (!left)
+            add_zy_kernel<double2><<<blocks(N), kThreads, 0, s>>>(N, W.Z, N, j, W.y, X);
+        else if (lowp)
+            add_zy_kernel<float2><<<blocks(N), kThreads, 0, s>>>(N, W.V32, N, j, W.y, X);
+        else
+            add_zy_kernel<double2><<<blocks(N), kThreads, 0, s>>>(N, W.V, N, j, W.y, X);
         CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(s));

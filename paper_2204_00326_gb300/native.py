@@ -23,6 +23,8 @@ DAFMM_ENOTCONV = 3
 DAFMM_EBREAKDOWN = 4
 DAFMM_ETIMEOUT = 5
 DAFMM_ECUDA = 6
+DAFMM_PREC_RIGHT = 0
+DAFMM_PREC_LEFT = 1
 DAFMM_FP64 = 0
 DAFMM_MIXED = 1
 
@@ -105,7 +107,8 @@ class gmres_opts(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("history", ctypes.POINTER(ctypes.c_double)),
         ("history_len", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("side", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
@@ -325,13 +328,15 @@ def dafmm_profile_read(ops: int) -> dafmm_profile_t:
 
 
 def gmres_solve(ops: int, f, x, tol: float = 1e-8, precision: int = DAFMM_FP64, restart: int = 50, max_iters: int = 1000,
-                inner_tol: float = 1e-5, M: int | None = None, stream=None, history_len: int = 0):
+                inner_tol: float = 1e-5, M: int | None = None, stream=None, history_len: int = 0, side: int = 0):
     """Solve A x = f (x holds the initial guess on entry).  Returns (status, stats, history).
 
+    side: DAFMM_PREC_RIGHT (0) or DAFMM_PREC_LEFT (1) preconditioning by M.
     status is DAFMM_OK or DAFMM_ENOTCONV (not converged within max_iters); other
     failures raise DafmmError.
     """
     o = gmres_opts()
+    o.side = side
     o.restart = restart
     o.max_iters = max_iters
     o.tol = tol

@@ -171,6 +171,32 @@ def test_gmres_hodlr_preconditioned_needs_fewer_iterations(N, grid32):
     N.hodlr_destroy(M)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gmres_left_preconditioning_matches_dense_lu(N, grid32, precision):
+    """The paper's side (M^{-1} A x = M^{-1} f, Eq. hybrid): the same FP64
+    true-residual stopping rule, the same solution as the dense LU solve, and
+    HODLR still cuts the iteration count."""
+    w, op, A, f = grid32
+    prec = N.DAFMM_FP64 if precision == "fp64" else N.DAFMM_MIXED
+    M = N.hodlr_factor(op.ops, rank=15, leaf_size=64)
+    try:
+        rc, st, x = _solve(N, op, f, tol=1e-10, precision=prec, M=M, side=N.DAFMM_PREC_LEFT, max_iters=500)
+        assert rc == N.DAFMM_OK and st.converged == 1 and st.rel_residual <= 1e-10
+        assert np.linalg.norm(A @ x - f) / np.linalg.norm(f) < 1e-10 + 1e-10
+        assert _rel(x, O.lu_solve(A, f)) < 1e-7
+        rc0, st0, _ = _solve(N, op, f, tol=1e-10, precision=prec, max_iters=500)
+        assert st.iterations < st0.iterations
+        assert st.precond_applies >= st.iterations
+    finally:
+        N.hodlr_destroy(M)
+
+
+def test_gmres_side_argument_checked(N, grid32):
+    w, op, A, f = grid32
+    with pytest.raises(N.DafmmError):
+        _solve(N, op, f, tol=1e-8, side=2)
+
+
 def test_gmres_reports_not_converged(N, grid32):
     w, op, A, f = grid32
     rc, st, x = _solve(N, op, f, tol=1e-12, max_iters=3, restart=3)

@@ -234,6 +234,15 @@ int build_nca_operators(dafmm_tree* tree, const double* q_dev, void* stream, daf
 int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v_dev, double* out_dev, int precision, void* stream);
 
 /*
+ * dafmm_potential -- out = K~ v: the volume potential V[v] of Eq. 5 at the N
+ * nodes, discretised as in Eq. 13 and applied by the same DAFMM passes (the
+ * scattered field u_scat = V[psi] from the solution psi, as the paper
+ * evaluates it on the grid).  No identity and no kappa^2 q.  Arguments,
+ * layouts and errors as dafmm_matvec; launched directly (no graph replay).
+ */
+int dafmm_potential(const dafmm_ops* ops, int nrhs, const double* v_dev, double* out_dev, int precision, void* stream);
+
+/*
  * gmres_solve -- solve A psi = f (Eq. 12a) with restarted flexible GMRES
  * (Saad), right-preconditioned by the HODLR approximation M when M != NULL
  * (the Hybrid solver, Eq. hybrid; right rather than left preconditioning so

@@ -1340,9 +1340,13 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
             ai = (double)eh + (double)el;
         }
         const size_t gi = ((size_t)leaf * 16 + i) * nrhs + r;
-        const double2 vv = v[gi];
-        const double sc = k2 * q[(size_t)leaf * 16 + i];
-        out[gi] = make_double2(vv.x + sc * (double)ar, vv.y + sc * (double)ai);
+        if (q == nullptr) {
+            out[gi] = make_double2((double)ar, (double)ai);  // the potential K v alone
+        } else {
+            const double2 vv = v[gi];
+            const double sc = k2 * q[(size_t)leaf * 16 + i];
+            out[gi] = make_double2(vv.x + sc * (double)ar, vv.y + sc * (double)ai);
+        }
     }
 }
 
@@ -1406,7 +1410,7 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
     if (grp == 0) {
         const int t0 = li;  // 0 .. 16 kLeafPerCta - 1
         constexpr int kThr = 16 * kLeafPerCta;
-        if (leaf < nleaf) {
+        if (leaf < nleaf && q != nullptr) {
             vv = v[(size_t)leaf * 16 + i];
             qq = q[(size_t)leaf * 16 + i];
         }
@@ -1530,7 +1534,7 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
         const C a = part[0][li], b = part[1][li];
         const T sr = mine.x + a.x + b.x, si = mine.y + a.y + b.y;
         const size_t gi = (size_t)leaf * 16 + i;
-        const double sc = k2 * qq;
+        const double sc = q != nullptr ? k2 * qq : 1.0;  // q == nullptr: the potential K v alone
         out[gi] = make_double2(vv.x + sc * (double)sr, vv.y + sc * (double)si);
     }
 }
@@ -2215,7 +2219,7 @@ void run_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const double* 
         nleaf, d.nbr, nearp, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
         l2p ? (const C*)(sizeof(T) == 8 ? l2p->mdf : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr, nullptr,
         comp ? d.leafc.rowptr : nullptr, comp ? d.leafc.col : nullptr, comp ? d.leafc.moff : nullptr, comp ? d.leafc.rin : nullptr, cm,
-        comp ? d.lv[L - 1].Ri : 0, comp ? b.lc[L - 1] : nullptr, comp && L - 1 > t.top ? b.lcd[L - 1] : nullptr, (const double2*)v, d.q,
+        comp ? d.lv[L - 1].Ri : 0, comp ? b.lc[L - 1] : nullptr, comp && L - 1 > t.top ? b.lcd[L - 1] : nullptr, (const double2*)v, d.potential ? nullptr : d.q,
         t.prm.kappa * t.prm.kappa, (double2*)out, far ? d.fz.done : nullptr);
     CK(cudaGetLastError());
     mark(prof, 4, s);
@@ -2304,7 +2308,7 @@ void run_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, float2* v32, 
     leaf_batched_kernel<T><<<(unsigned)nleaf, 256, 0, s>>>(
         nleaf, nrhs, d.nbr, nearp, vin, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
         l2p ? (const C*)(sizeof(T) == 8 ? l2p->mdf : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr,
-        (const double2*)v, d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
+        (const double2*)v, d.potential ? nullptr : d.q, t.prm.kappa * t.prm.kappa, (double2*)out);
     CK(cudaGetLastError());
     mark(prof, 4, s);
 }
@@ -2643,6 +2647,23 @@ void capture(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, i
 }
 
 }  // namespace
+
+void apply_potential(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream)
+{
+    // the same passes with the leaf epilogue writing K v; launched directly (no graph)
+    if (nrhs < 1 || nrhs > kMaxRhs) fail(DAFMM_EBADARG, "nrhs must lie in 1..64");
+    if (t.L >= 64) fail(DAFMM_EBADARG, "tree too deep");
+    cudaGetLastError();
+    ensure_scratch(t, d, nrhs);
+    d.potential = true;
+    try {
+        run_eager(t, d, v, out, nrhs, precision, stream, false);
+    } catch (...) {
+        d.potential = false;
+        throw;
+    }
+    d.potential = false;
+}
 
 void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream)
 {

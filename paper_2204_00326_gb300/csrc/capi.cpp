@@ -248,6 +248,17 @@ int dafmm_matvec(const dafmm_ops* ops, int nrhs, const double* v, double* out, i
     });
 }
 
+int dafmm_potential(const dafmm_ops* ops, int nrhs, const double* v, double* out, int precision, void* stream)
+{
+    return guarded([&] {
+        if (!ops || !v || !out) fail(DAFMM_EBADARG, "NULL argument");
+        if (nrhs < 1) fail(DAFMM_EBADARG, "nrhs must be >= 1");
+        if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+        if (v == out) fail(DAFMM_EBADARG, "v and out must not overlap");
+        apply_potential(ops->tree->t, const_cast<dafmm_ops*>(ops)->dev, nrhs, v, out, precision, (cudaStream_t)stream);
+    });
+}
+
 int dafmm_matvec_noalloc(const dafmm_ops* ops, const double* v, double* out, int precision, void* stream)
 {
     return guarded([&] {

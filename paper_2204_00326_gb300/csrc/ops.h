@@ -118,6 +118,7 @@ struct OpsDev {
     int nrhs_cap = 0;           // scratch sized for this many right-hand sides
     int* err = nullptr;         // device flag: a bounded wait in a kernel gave up
     int stall_pass = -1;        // test support: the next fused launch waits for a row this pass never writes
+    bool potential = false;     // the leaf epilogue writes K v (apply_potential)
     // per-pass timing: 5 events per profiled call (start, up, m2l, down, leaf);
     // for a fused call the first interval holds the whole far field
     bool profile = false;
@@ -141,6 +142,8 @@ void profile_read(OpsDev& d, dafmm_profile_t& p);
 void ensure_scratch(const Tree& t, OpsDev& d, int nrhs);
 // out = v + kappa^2 q (K~ v), asynchronous on stream.
 void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream);
+// out = K~ v (the volume potential at the nodes, no identity and no kappa^2 q), same kernels.
+void apply_potential(const Tree& t, OpsDev& d, int nrhs, const double* v, double* out, int precision, cudaStream_t stream);
 // Same operator, one right-hand side, scratch in a static device array.
 void apply_matvec_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, int precision, cudaStream_t stream);
 // GMRES (gmres.cu); prec: z = M^{-1} v, or nullptr.

@@ -160,6 +160,7 @@ _sig = {
     "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
+    "dafmm_potential": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_set_contrast": ([_P, _P, _P], ctypes.c_int),
     "gmres_solve": ([_P, _P, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
     "hodlr_factor": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
@@ -273,6 +274,14 @@ def dafmm_matvec(ops: int, v, out, precision: int = DAFMM_FP64, stream=None) -> 
     if out.shape != v.shape:
         raise ValueError("v and out must have the same shape")
     _check(lib.dafmm_matvec(ops, nrhs, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
+
+
+def dafmm_potential(ops: int, v, out, precision: int = DAFMM_FP64, stream=None) -> None:
+    """out = K v: the volume potential at the nodes (the scattered field from psi)."""
+    nrhs = 1 if v.dim() == 1 else v.shape[1]
+    if out.shape != v.shape:
+        raise ValueError("v and out must have the same shape")
+    _check(lib.dafmm_potential(ops, nrhs, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20

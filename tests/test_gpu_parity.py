@@ -128,6 +128,26 @@ def test_mixed_matvec_grid128_sampled_rows(N, op128):
     assert _rel(out[rows], ref) < MIXED_TOL
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
+def test_potential_matches_oracle_rows(N, op128, precision, tol):
+    """dafmm_potential is K v (the scattered field V[psi] at the nodes): the
+    oracle's A with q = 1/kappa^2 is I + K, so (A v - v) on sampled rows is the
+    reference; and the operator application is v + kappa^2 q (K v)."""
+    w = W.GRID128_K40
+    prec = N.DAFMM_FP64 if precision == "fp64" else N.DAFMM_MIXED
+    rows = np.sort(np.random.default_rng(14).choice(w.N, 48, replace=False))
+    v = W.random_vector(w.N, 1, seed=15)[:, 0]
+    vd = torch.as_tensor(v, device="cuda")
+    kv = torch.empty_like(vd)
+    N.dafmm_potential(op128.ops, vd, kv, prec)
+    kvh = kv.cpu().numpy()
+    ref = O.matvec_rows(w.n_side, w.kappa, np.full(w.N, 1.0 / w.kappa ** 2), v, rows) - v[rows]
+    assert _rel(kvh[rows], ref) < tol
+    av = op128.matvec(vd, precision=prec).cpu().numpy()
+    assert _rel(av, v + w.kappa ** 2 * op128.q * kvh) < (1e-12 if precision == "fp64" else 1e-6)
+    op128.sync()
+
+
 def test_matvec_is_linear_and_repeatable(N, op128):
     w = W.GRID128_K40
     a = torch.as_tensor(W.random_vector(w.N, 1, seed=8)[:, 0], device="cuda")

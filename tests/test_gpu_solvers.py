@@ -140,6 +140,26 @@ def test_hodlr_barrier_timeout_is_reported_and_the_handle_recovers(N, grid32):
         N.hodlr_destroy(M)
 
 
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_hodlr_direct_solver(N, grid32, tol):
+    """HODLR as a direct solver (the paper's third solver): ACA to a tolerance,
+    the Woodbury inverse applied once, no GMRES.  The residual against the
+    oracle's dense A follows the compression tolerance."""
+    w, op, A, f = grid32
+    M = N.hodlr_factor(op.ops, rank=0, tol=tol, leaf_size=64)
+    try:
+        fd = torch.as_tensor(f, device="cuda")
+        x = torch.empty_like(fd)
+        N.hodlr_solve(M, fd, x, N.DAFMM_FP64)
+        N.hodlr_sync(M)
+        xh = x.cpu().numpy()
+        res = np.linalg.norm(A @ xh - f) / np.linalg.norm(f)
+        assert res < 100 * tol, res
+        assert _rel(xh, O.lu_solve(A, f)) < 1e3 * tol
+    finally:
+        N.hodlr_destroy(M)
+
+
 def _solve(N, op, f, **kw):
     x = torch.zeros(op.N, dtype=torch.complex128, device="cuda")
     rc, st, hist = N.gmres_solve(op.ops, torch.as_tensor(f, device="cuda"), x, **kw)

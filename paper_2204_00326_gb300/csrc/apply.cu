@@ -1595,14 +1595,11 @@ void upload_bsr(BsrHost& h, BsrDev& d)
     upload_vec(h.moff, &d.moff);
     const size_t n = h.mats.size();
     // two spare entries: a bulk copy rounds its window out to 16-byte words
-    dev_alloc((double2**)&d.m64, sizeof(double2) * (n + 2));
     dev_alloc((float2**)&d.m32, sizeof(float2) * (n + 4));
     dev_alloc((float4**)&d.mdf, sizeof(float4) * (n + 2));
-    CK(cudaMemset(d.m64, 0, sizeof(double2) * (n + 2)));
     CK(cudaMemset(d.m32, 0, sizeof(float2) * (n + 4)));
     CK(cudaMemset(d.mdf, 0, sizeof(float4) * (n + 2)));
     if (n) {
-        CK(cudaMemcpy(d.m64, h.mats.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
         std::vector<float2> f(n);
         for (size_t k = 0; k < n; k++) f[k] = make_float2((float)h.mats[k].real(), (float)h.mats[k].imag());
         CK(cudaMemcpy(d.m32, f.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
@@ -1626,7 +1623,6 @@ void free_bsr(BsrDev& d)
     cudaFree(d.col);
     cudaFree(d.rin);
     cudaFree(d.moff);
-    cudaFree(d.m64);
     cudaFree(d.m32);
     cudaFree(d.mdf);
     d = BsrDev();

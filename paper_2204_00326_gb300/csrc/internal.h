@@ -109,7 +109,6 @@ struct BsrDev {
     int* rin = nullptr;
     long* moff = nullptr;
     int* rowptr = nullptr;
-    void* m64 = nullptr;  // double2 blocks
     void* m32 = nullptr;  // float2 blocks
     void* mdf = nullptr;  // float4 blocks {re hi, im hi, re lo, im lo}: complex128 as float pairs
 };

@@ -12,8 +12,9 @@ application is timed in the same run and reported beside it.
 same workload, a bounded sample of rows per step, on the host cores.
 
 Multi-GPU runs (torchrun) run one independent replica per rank: a single
-problem has no data-parallel split, so value = all ranks'
-unknowns / max-over-ranks time and scaling is "weak".
+problem has no data-parallel split (it would exchange multipoles at every
+level), so value = all ranks' unknowns / max-over-ranks time and scaling is
+"weak".
 """
 from __future__ import annotations
 

@@ -61,7 +61,7 @@ extern "C" {
 
 /* Parameters of the discretisation and of the compression (Section 3-4). */
 typedef struct dafmm_params {
-    int p;            /* Chebyshev nodes per leaf side; this build supports p = 4 */
+    int p;            /* Chebyshev nodes per leaf side; the library supports p = 4 */
     double kappa;     /* wavenumber kappa > 0 (Eq. 1) */
     double T;         /* a box of half-width w is high-frequency iff (kappa w)^2 > T
                          (Section 3; the paper leaves T open, 16 is the default) */

@@ -92,6 +92,12 @@ def test_null_and_device_errors_are_status_codes():
     lib = N.lib
     assert lib.build_tree(None, 16, -1.0, 1.0, None) == N.DAFMM_EBADARG
     assert lib.dafmm_matvec(None, 1, None, None, 0, None) == N.DAFMM_EBADARG
+    assert lib.dafmm_potential(None, 1, None, None, 0, None) == N.DAFMM_EBADARG
+    assert lib.hodlr_sync(None, None) == N.DAFMM_EBADARG
+    assert lib.hodlr_set_ctas(None, 0) == N.DAFMM_EBADARG
+    assert lib.hodlr_debug_stall(None) == N.DAFMM_EBADARG
+    assert lib.hodlr_solve(None, 1, None, None, 0, None) == N.DAFMM_EBADARG
+    assert lib.gmres_solve(None, None, None, None, None, None, None) == N.DAFMM_EBADARG
     buf = ctypes.create_string_buffer(256)
     assert lib.dafmm_last_error(buf, 256) == N.DAFMM_EBADARG
     assert b"NULL" in buf.value

@@ -252,15 +252,25 @@ int dafmm_potential(const dafmm_ops* ops, int nrhs, const double* v_dev, double*
  * Hessenberg matrix, Givens rotations, preconditioned basis and x are FP64
  * on the device; the Arnoldi basis is complex128 in FP64 cycles and
  * complex64 in the inner cycles of DAFMM_MIXED.  A zero initial guess takes
- * r = f without an application.  f_dev: N complex128 (not modified); x_dev:
- * N complex128, in: initial guess, out: solution.  Its Krylov workspace is
- * kept on the ops handle between calls (grown when N or m grows); calls on
- * one handle must be ordered.  Synchronises the stream.
- * Returns DAFMM_OK when converged, DAFMM_ENOTCONV when max_iters was reached
- * (x holds the last iterate, st the residual), DAFMM_EBADARG, DAFMM_ENOMEM,
- * DAFMM_ECUDA.
+ * r = f without an application.  f_dev: N x nrhs complex128 (not modified);
+ * x_dev: N x nrhs complex128, in: initial guess, out: solution (both
+ * [N][nrhs], right-hand side fastest).  nrhs in 1..64: several right-hand
+ * sides are solved together by nrhs independent GMRES processes in lockstep,
+ * each step applying A (and M) to all columns in one batched application;
+ * every column has its own Hessenberg matrix, rotations, inner tolerance and
+ * FP64 true-residual stopping rule (a column that has converged stops
+ * contributing; its later basis vectors are zero).  st: nrhs entries, one
+ * per column (matvecs and precond_applies count batched applications,
+ * iterations the steps that column used).  With several right-hand sides,
+ * opts->history receives the largest relative residual over the columns.
+ * Its Krylov workspace is kept on the ops handle between calls (grown when
+ * N, nrhs or m grows); calls on one handle must be ordered.  Synchronises
+ * the stream.
+ * Returns DAFMM_OK when every column converged, DAFMM_ENOTCONV when
+ * max_iters was reached (x holds the last iterates, st the residuals),
+ * DAFMM_EBADARG (nrhs outside 1..64, ...), DAFMM_ENOMEM, DAFMM_ECUDA.
  */
-int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, const double* f_dev, double* x_dev, const gmres_opts* opts, gmres_stats* st,
+int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, int nrhs, const double* f_dev, double* x_dev, const gmres_opts* opts, gmres_stats* st,
                 void* stream);
 
 /*
@@ -281,13 +291,16 @@ int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, const double* f_dev, doubl
 int hodlr_factor(const dafmm_ops* ops, int rank, double tol, int leaf_size, dafmm_hodlr** out);
 
 /*
- * hodlr_solve -- x = A~^{-1} b for one right-hand side (nrhs must be 1):
- * leaf inverses, then per level from the leaves up t = W x, s = S^{-1} t,
+ * hodlr_solve -- x = A~^{-1} b for nrhs right-hand sides (1..64): leaf
+ * inverses, then per level from the leaves up t = W x, s = S^{-1} t,
  * x -= Ut s (recursive Sherman-Morrison-Woodbury, Section 6).  Cost
- * O(r N log N).  One cooperative launch whose CTAs meet at a grid barrier
- * per level; each barrier wait has a limit (about 0.2 s), after which the
- * launch sets the handle's error flag and returns (see hodlr_sync).
- * b_dev, x_dev: N complex128 on the device; x_dev == b_dev is allowed.
+ * O(r N log N) per right-hand side.  One right-hand side: one cooperative
+ * launch whose CTAs meet at a grid barrier per level; each barrier wait has
+ * a limit (about 0.2 s), after which the launch sets the handle's error flag
+ * and returns (see hodlr_sync).  Several: ordinary launches per level (no
+ * device waits), the factors read once for all columns; ranks up to 256.
+ * b_dev, x_dev: N x nrhs complex128 on the device, [N][nrhs] (right-hand side
+ * fastest); x_dev == b_dev is allowed.
  * precision: DAFMM_FP64 (factors as float pairs, double-float arithmetic,
  * result rounded to double), or DAFMM_MIXED (complex64 factors and
  * arithmetic); boundary vectors are complex128.  Asynchronous on stream.  Calls on one
@@ -352,10 +365,15 @@ int hodlr_destroy(dafmm_hodlr* M);
  * device array of DAFMM_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading
  * the library holds until the process exits.  The first call on a device
  * resolves that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture.  Every call on a
+ * current; make that first call before any stream capture.  The address is
+ * cached for the life of the process: it stays valid while the device's
+ * primary context lives, so do not call this entry point after the caller has
+ * reset the device (cudaDeviceReset) or torn its primary context down.  Every call on a
  * device shares the array and clears the part it uses, so calls whose kernels
  * overlap in time on one device race and must be ordered by the caller (one
- * stream, or events).  The operator itself (built by build_nca_operators)
+ * stream, or events).  The call also uses the ops handle's pass counters,
+ * like dafmm_matvec: on one handle, a dafmm_matvec_noalloc and a dafmm_matvec
+ * must not overlap in time either.  The operator itself (built by build_nca_operators)
  * must already exist; v_dev and out_dev are the caller's N complex128 device
  * vectors and must not overlap.
  * Errors: DAFMM_EBADARG when the problem needs more scratch than the array

@@ -2490,6 +2490,8 @@ void profile_read(OpsDev& d, dafmm_profile_t& p)
 void free_ops(OpsDev& d)
 {
     gmres_work_free(d.gw);
+    gmres_many_free(d.gm);
+    d.gm = nullptr;
     d.gw = nullptr;
     for (cudaEvent_t e : d.events) cudaEventDestroy(e);
     d.events.clear();
@@ -2761,8 +2763,9 @@ void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs,
 // own pool (a cudaMalloc there can fail or fragment the pool), hot loops that
 // cannot afford cudaMalloc's implicit device synchronisation, and deployments
 // that must fix all memory before they start.  For them the scratch of one
-// single-RHS application (coefficients, chunk partials, the complex64 copy of
-// the input) lives in this fixed device array instead of the handle's
+// single-RHS application (chunk partials, and per level the multipoles, the
+// locals written by M2L and the locals written by the parent's L2L) lives in
+// this fixed device array instead of the handle's
 // grow-on-demand buffers.  Every GPU that loads the library holds the array
 // until the process exits; all calls on a device share it, so calls whose
 // kernels overlap in time on that device race.
@@ -2805,8 +2808,8 @@ void run_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, c
     size_t need = align256(sizeof(C) * std::max<size_t>(d.part_elems, 1));
     if (far)
         for (int nu = t.top; nu <= L; nu++)
-            need += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ro) +
-                    2 * align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ri);
+            need += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * std::max(d.lv[nu].Ro, 1)) +
+                    2 * align256(sizeof(C) * (size_t)t.lv[nu].nslot() * std::max(d.lv[nu].Ri, 1));
     if (need > (size_t)DAFMM_NOALLOC_SCRATCH_BYTES)
         fail(DAFMM_EBADARG, "problem needs " + std::to_string(need) + " bytes of scratch; the allocation-free path holds " +
                                 std::to_string((size_t)DAFMM_NOALLOC_SCRATCH_BYTES) + " (use dafmm_matvec)");
@@ -2820,11 +2823,12 @@ void run_noalloc(const Tree& t, const OpsDev& d, const double* v, double* out, c
     if (far)
         for (int nu = t.top; nu <= L; nu++) {
             b.mp[nu] = (C*)(base + off);
-            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ro);
+            // at least one row per slot even at rank 0, as in the handle's own buffers
+            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * std::max(d.lv[nu].Ro, 1));
             b.lc[nu] = (C*)(base + off);
-            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ri);
+            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * std::max(d.lv[nu].Ri, 1));
             b.lcd[nu] = (C*)(base + off);
-            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * d.lv[nu].Ri);
+            off += align256(sizeof(C) * (size_t)t.lv[nu].nslot() * std::max(d.lv[nu].Ri, 1));
         }
     run_fused<T>(t, d, b, v, out, s, nullptr);
 }

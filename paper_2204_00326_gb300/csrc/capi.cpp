@@ -315,22 +315,25 @@ void learned_prec(const void* P, const double* v, double* z, int precision, cuda
 }
 }  // namespace
 
-int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, const double* f, double* x, const gmres_opts* opts, gmres_stats* st,
+int gmres_solve(dafmm_ops* ops, const dafmm_hodlr* M, int nrhs, const double* f, double* x, const gmres_opts* opts, gmres_stats* st,
                 void* stream)
 {
     int code = DAFMM_OK;
     int r = guarded([&] {
         check_gmres(ops, f, x, opts, st);
-        PrecFn prec = nullptr;
-        if (M) {
-            if (hodlr_tree(M) != ops->tree) fail(DAFMM_EBADARG, "the preconditioner was built on another tree");
-            prec = hodlr_prec;
-        }
-        code = gmres_run(ops->tree->t, ops->dev, M, prec, f, x, *opts, *st, (cudaStream_t)stream);
+        if (nrhs < 1 || nrhs > 64) fail(DAFMM_EBADARG, "gmres_solve takes 1 to 64 right-hand sides");
+        if (M && hodlr_tree(M) != ops->tree) fail(DAFMM_EBADARG, "the preconditioner was built on another tree");
+        if (nrhs == 1)
+            code = gmres_run(ops->tree->t, ops->dev, M, M ? hodlr_prec : nullptr, f, x, *opts, *st, (cudaStream_t)stream);
+        else
+            code = gmres_run_many(ops->tree->t, ops->dev, M, M ? hodlr_prec_many : nullptr, nrhs, f, x, *opts, st, (cudaStream_t)stream);
         if (M && hodlr_check(M, (cudaStream_t)stream) == DAFMM_ETIMEOUT)
             fail(DAFMM_ETIMEOUT, "a wait of the HODLR application gave up; the solution is undefined");
-        if (code == DAFMM_ENOTCONV)
-            fail(DAFMM_ENOTCONV, "GMRES reached max_iters at relative residual " + std::to_string(st->rel_residual));
+        if (code == DAFMM_ENOTCONV) {
+            double worst = 0;
+            for (int c = 0; c < nrhs; c++) worst = std::max(worst, st[c].rel_residual);
+            fail(DAFMM_ENOTCONV, "GMRES reached max_iters at relative residual " + std::to_string(worst));
+        }
     });
     return r;
 }
@@ -349,9 +352,12 @@ int hodlr_solve(const dafmm_hodlr* M, int nrhs, const double* b, double* x, int 
 {
     return guarded([&] {
         if (!M || !b || !x) fail(DAFMM_EBADARG, "NULL argument");
-        if (nrhs != 1) fail(DAFMM_EBADARG, "hodlr_solve applies one right-hand side per call");
+        if (nrhs < 1 || nrhs > 64) fail(DAFMM_EBADARG, "hodlr_solve takes 1 to 64 right-hand sides");
         if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
-        hodlr_apply(M, b, x, precision, (cudaStream_t)stream);
+        if (nrhs == 1)
+            hodlr_apply(M, b, x, precision, (cudaStream_t)stream);
+        else
+            hodlr_apply_many(M, nrhs, b, x, precision, (cudaStream_t)stream);
     });
 }
 

@@ -423,6 +423,237 @@ __global__ void init_g_kernel(int m, const double2* __restrict__ rn2, double2* _
 
 unsigned blocks(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+// ------------------------------------------------------------------------
+// Several right-hand sides: nrhs independent GMRES processes in lockstep.
+// One Arnoldi step applies the preconditioner and the operator to all the
+// current basis vectors at once (one batched application each), then every
+// column is orthogonalised against its own basis (classical Gram-Schmidt
+// twice) by kernels over [N][nrhs] blocks whose threads take consecutive
+// columns, and takes its own Givens step.  A column ends its cycle when its
+// own estimate reaches its inner tolerance (later steps of that column are
+// not used) and leaves the solve when its own FP64 true residual reaches
+// tol.  Sums run in a fixed order (results do not depend on timing).
+
+constexpr int kMT = 256;     // threads of the several-column kernels
+constexpr int kMB = 64;      // columns at most
+constexpr int kMRows = 256;  // rows per CTA of the reductions
+constexpr int kMK = 8;       // basis vectors per CTA of the dot products
+
+// w[e] = (w64 ? w64[e] : w[e]) - sum_{k < nk} V_k[e] h[k][c], c = e mod B,
+// for the N B entries e of [N][B] vectors (V_k at V + k N B).
+template <typename T>
+__global__ void many_update_kernel(long NB, int B, const typename CT<T>::t* __restrict__ V, int nk, const double2* __restrict__ h,
+                                   typename CT<T>::t* __restrict__ w, const double2* __restrict__ w64)
+{
+    using C = typename CT<T>::t;
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= NB) return;
+    const int c = (int)(e % B);
+    C a = w64 ? from64<T>(w64[e]) : w[e];
+#pragma unroll 4
+    for (int k = 0; k < nk; k++) {
+        const C p = cmul_t(V[(size_t)k * NB + e], from64<T>(__ldg(&h[(size_t)k * B + c])));
+        a.x -= p.x;
+        a.y -= p.y;
+    }
+    w[e] = a;
+}
+
+// part[k][rb][c] = sum over the rows n of block rb of conj(V_k[n][c]) w[n][c],
+// for k in [kMK blockIdx.y, + kMK) below nk.  Products and sums in T; the
+// four row groups of a block are added in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kMT) many_dots_kernel(long N, int B, const typename CT<T>::t* __restrict__ V, int nk,
+                                                        const typename CT<T>::t* __restrict__ w, double2* __restrict__ part)
+{
+    using C = typename CT<T>::t;
+    __shared__ double2 red[4][kMK][kMB];
+    const int tid = threadIdx.x, c = tid % kMB, rg = tid / kMB;
+    const long r0 = (long)blockIdx.x * kMRows, r1 = min(N, r0 + kMRows);
+    const int k0 = blockIdx.y * kMK, kn = min(kMK, nk - k0);
+    const long NB = N * B;
+    C acc[kMK];
+#pragma unroll
+    for (int u = 0; u < kMK; u++) acc[u].x = acc[u].y = 0;
+    if (c < B)
+        for (long n = r0 + rg; n < r1; n += 4) {
+            const C wv = w[n * B + c];
+#pragma unroll
+            for (int u = 0; u < kMK; u++)
+                if (u < kn) {
+                    const C p = cconjmul_t(V[(size_t)(k0 + u) * NB + n * B + c], wv);
+                    acc[u].x += p.x;
+                    acc[u].y += p.y;
+                }
+        }
+#pragma unroll
+    for (int u = 0; u < kMK; u++) red[rg][u][c] = make_double2((double)acc[u].x, (double)acc[u].y);
+    __syncthreads();
+    for (int e = tid; e < kMK * kMB; e += kMT) {
+        const int u = e / kMB, cc = e - u * kMB;
+        if (u < kn && cc < B) {
+            double2 s = red[0][u][cc];
+            for (int g = 1; g < 4; g++) {
+                s.x += red[g][u][cc].x;
+                s.y += red[g][u][cc].y;
+            }
+            part[((size_t)(k0 + u) * gridDim.x + blockIdx.x) * B + cc] = s;
+        }
+    }
+}
+
+// out[k][c] = sum over rb of part[k][rb][c] (block k; a fixed order).
+__global__ void __launch_bounds__(kMT) many_reduce_kernel(int nrb, int B, const double2* __restrict__ part, double2* __restrict__ out)
+{
+    __shared__ double2 red[4][kMB];
+    const int tid = threadIdx.x, c = tid % kMB, g = tid / kMB, k = blockIdx.x;
+    double2 a = make_double2(0, 0);
+    if (c < B)
+        for (int rb = g; rb < nrb; rb += 4) {
+            const double2 p = part[((size_t)k * nrb + rb) * B + c];
+            a.x += p.x;
+            a.y += p.y;
+        }
+    red[g][c] = a;
+    __syncthreads();
+    if (g == 0 && c < B)
+        out[(size_t)k * B + c] =
+            make_double2(red[0][c].x + red[1][c].x + red[2][c].x + red[3][c].x, red[0][c].y + red[1][c].y + red[2][c].y + red[3][c].y);
+}
+
+// Givens bookkeeping of step j, one thread per column c: column j of c's
+// Hessenberg matrix is h1 + h2 with |w| below it; the previous rotations,
+// then a new one zeroing the subdiagonal; g updated, res[c] = |g[j+1]|.
+// H: per column (m+1) x m column-major; cs, sn: per column m; g: m + 1.
+__global__ void many_givens_kernel(int j, int m, int B, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                                   const double2* __restrict__ wn2, double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ sn,
+                                   double2* __restrict__ g, double* __restrict__ res)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B) return;
+    double2* col = H + ((size_t)c * m + j) * (m + 1);
+    double2* csc = cs + (size_t)c * m;
+    double2* snc = sn + (size_t)c * m;
+    double2* gc = g + (size_t)c * (m + 1);
+    for (int k = 0; k <= j; k++) col[k] = make_double2(h1[(size_t)k * B + c].x + h2[(size_t)k * B + c].x, h1[(size_t)k * B + c].y + h2[(size_t)k * B + c].y);
+    col[j + 1] = make_double2(sqrt(fmax(wn2[c].x, 0.0)), 0.0);
+    for (int k = 0; k < j; k++) {
+        const double cc = csc[k].x;
+        const double2 s = snc[k];
+        const double2 a = col[k], b = col[k + 1];
+        const double2 sb = cmul(s, b);
+        const double2 csa = make_double2(s.x * a.x + s.y * a.y, s.x * a.y - s.y * a.x);  // conj(s) a
+        col[k] = make_double2(cc * a.x + sb.x, cc * a.y + sb.y);
+        col[k + 1] = make_double2(-csa.x + cc * b.x, -csa.y + cc * b.y);
+    }
+    const double2 a = col[j], b = col[j + 1];
+    const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
+    double cc;
+    double2 s;
+    if (nb == 0.0) {
+        cc = 1.0;
+        s = make_double2(0, 0);
+    } else if (na == 0.0) {
+        cc = 0.0;
+        s = make_double2(b.x / nb, -b.y / nb);
+    } else {
+        const double t = hypot(na, nb);
+        cc = na / t;
+        const double2 ua = make_double2(a.x / na, a.y / na);
+        s = make_double2((ua.x * b.x + ua.y * b.y) / t, (ua.y * b.x - ua.x * b.y) / t);
+    }
+    csc[j] = make_double2(cc, 0.0);
+    snc[j] = s;
+    const double2 sb = cmul(s, b);
+    col[j] = make_double2(cc * a.x + sb.x, cc * a.y + sb.y);
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = gc[j];
+    const double2 csg = make_double2(s.x * gj.x + s.y * gj.y, s.x * gj.y - s.y * gj.x);
+    gc[j] = make_double2(cc * gj.x, cc * gj.y);
+    gc[j + 1] = make_double2(-csg.x, -csg.y);
+    res[c] = hypot(gc[j + 1].x, gc[j + 1].y);
+}
+
+// out[e] = a[e] / |column c| (0 for a zero norm or an inactive column), a
+// read from a (T) or a64 (complex128); written to out (T) and, when given,
+// out64 (complex128).
+template <typename T>
+__global__ void many_scale_kernel(long NB, int B, const typename CT<T>::t* __restrict__ a, const double2* __restrict__ a64,
+                                  const double2* __restrict__ nrm2, const int* __restrict__ active, typename CT<T>::t* __restrict__ out,
+                                  double2* __restrict__ out64)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= NB) return;
+    const int c = (int)(e % B);
+    const double n = sqrt(fmax(nrm2[c].x, 0.0));
+    const double sc = (n > 0 && active[c]) ? 1.0 / n : 0.0;
+    const double2 v = a64 ? a64[e] : make_double2((double)a[e].x, (double)a[e].y);
+    const double2 o = make_double2(v.x * sc, v.y * sc);
+    out[e] = from64<T>(o);
+    if (out64) out64[e] = o;
+}
+
+// g[c] = [|r0_c|, 0, ..., 0] for active columns, zero otherwise.
+__global__ void many_init_g_kernel(int m, int B, const double2* __restrict__ rn2, const int* __restrict__ active, double2* __restrict__ g)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B * (m + 1)) return;
+    const int c = e / (m + 1), k = e - c * (m + 1);
+    g[e] = (k == 0 && active[c]) ? make_double2(sqrt(fmax(rn2[c].x, 0.0)), 0.0) : make_double2(0, 0);
+}
+
+// Back substitution of column blockIdx.x: H_c[0:n_c, 0:n_c] y_c = g_c[0:n_c].
+__global__ void __launch_bounds__(kMaxM) many_backsolve_kernel(int m, const int* __restrict__ nstop, const double2* __restrict__ H,
+                                                               const double2* __restrict__ g, double2* __restrict__ y)
+{
+    __shared__ double2 yi;
+    const int c = blockIdx.x, t = threadIdx.x, n = nstop[c];
+    const double2* Hc = H + (size_t)c * m * (m + 1);
+    double2* yc = y + (size_t)c * m;
+    double2 gt = t < n ? g[(size_t)c * (m + 1) + t] : make_double2(0, 0);
+    for (int i = n - 1; i >= 0; i--) {
+        if (t == i) {
+            const double2 d = Hc[(size_t)i * (m + 1) + i];
+            const double dd = d.x * d.x + d.y * d.y;
+            const double2 v = dd > 0 ? make_double2((gt.x * d.x + gt.y * d.y) / dd, (gt.y * d.x - gt.x * d.y) / dd) : make_double2(0, 0);
+            yc[i] = v;
+            yi = v;
+        }
+        __syncthreads();
+        if (t < i) {
+            const double2 p = cmul(Hc[(size_t)i * (m + 1) + t], yi);
+            gt.x -= p.x;
+            gt.y -= p.y;
+        }
+        __syncthreads();
+    }
+}
+
+// x[e] += sum_{k < n_c} Z_k[e] y_c[k] (Z complex128 or complex64, Z_k at Z + k N B).
+template <typename C>
+__global__ void many_add_zy_kernel(long NB, int B, int m, const C* __restrict__ Z, const int* __restrict__ nstop, const double2* __restrict__ y,
+                                   double2* __restrict__ x)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= NB) return;
+    const int c = (int)(e % B), n = nstop[c];
+    double2 a = x[e];
+    for (int k = 0; k < n; k++) {
+        const C z = Z[(size_t)k * NB + e];
+        const double2 p = cmul(make_double2((double)z.x, (double)z.y), y[(size_t)c * m + k]);
+        a.x += p.x;
+        a.y += p.y;
+    }
+    x[e] = a;
+}
+
+// Columns c with flag[c] set are zeroed.
+__global__ void many_zero_cols_kernel(long NB, int B, const int* __restrict__ flag, double2* __restrict__ x)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e < NB && flag[e % B]) x[e] = make_double2(0, 0);
+}
+
 }  // namespace
 
 // Workspace of one operator handle, kept between solves (grown on demand).
@@ -683,6 +914,289 @@ int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double
     st.rel_residual = rel;
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return st.converged ? DAFMM_OK : DAFMM_ENOTCONV;
+}
+
+
+// Workspace of the several-right-hand-side solve (vectors [N][B], bases
+// [k][N][B]), kept on the handle and grown on demand.
+struct GmresMany {
+    long N = 0;
+    int B = 0, m = 0, nrb = 0;
+    bool v64 = false, v32 = false, z = false;  // which bases are allocated
+    double2 *V64 = nullptr, *Z = nullptr, *w64 = nullptr, *r = nullptr, *tv = nullptr, *zin = nullptr, *vcur = nullptr;
+    float2 *V32 = nullptr, *w32 = nullptr;
+    double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h1 = nullptr, *h2 = nullptr, *part = nullptr,
+            *sc = nullptr;  // sc: [4][B] squared column norms
+    double* res = nullptr;
+    double* res_host = nullptr;
+    int *nstop = nullptr, *active = nullptr, *flag = nullptr;
+    void release()
+    {
+        for (void* p : {(void*)V64, (void*)Z, (void*)w64, (void*)r, (void*)tv, (void*)zin, (void*)vcur, (void*)V32, (void*)w32, (void*)H,
+                        (void*)cs, (void*)sn, (void*)g, (void*)y, (void*)h1, (void*)h2, (void*)part, (void*)sc, (void*)res, (void*)nstop,
+                        (void*)active, (void*)flag})
+            cudaFree(p);
+        if (res_host) cudaFreeHost(res_host);
+        *this = GmresMany();
+    }
+};
+
+namespace {
+
+GmresMany& many_workspace(GmresMany& W, long N, int B, int m, bool need64, bool need32, bool needZ)
+{
+    if (!(W.N == N && W.B == B && W.m >= m)) {
+        W.release();
+        W.N = N;
+        W.B = B;
+        W.m = m;
+        W.nrb = (int)((N + kMRows - 1) / kMRows);
+        const size_t NB = (size_t)N * B;
+        dalloc(&W.w64, sizeof(double2) * NB);
+        dalloc(&W.r, sizeof(double2) * NB);
+        dalloc(&W.tv, sizeof(double2) * NB);
+        dalloc(&W.zin, sizeof(double2) * NB);
+        dalloc(&W.H, sizeof(double2) * B * (size_t)(m + 1) * m);
+        dalloc(&W.cs, sizeof(double2) * B * (size_t)m);
+        dalloc(&W.sn, sizeof(double2) * B * (size_t)m);
+        dalloc(&W.g, sizeof(double2) * B * (size_t)(m + 1));
+        dalloc(&W.y, sizeof(double2) * B * (size_t)m);
+        dalloc(&W.h1, sizeof(double2) * B * (size_t)(m + 1));
+        dalloc(&W.h2, sizeof(double2) * B * (size_t)(m + 1));
+        dalloc(&W.part, sizeof(double2) * B * (size_t)(m + 1) * W.nrb);
+        dalloc(&W.sc, sizeof(double2) * 4 * B);
+        dalloc(&W.res, sizeof(double) * B);
+        dalloc(&W.nstop, sizeof(int) * B);
+        dalloc(&W.active, sizeof(int) * B);
+        dalloc(&W.flag, sizeof(int) * B);
+        if (cudaMallocHost(&W.res_host, sizeof(double) * B) != cudaSuccess) {
+            cudaGetLastError();
+            fail(DAFMM_ENOMEM, "pinned host allocation for GMRES failed");
+        }
+    }
+    const size_t NB = (size_t)N * B;
+    if (need64 && !W.v64) {
+        dalloc(&W.V64, sizeof(double2) * NB * (W.m + 1));
+        W.v64 = true;
+    }
+    if (need32 && !W.v32) {
+        dalloc(&W.V32, sizeof(float2) * NB * (W.m + 1));
+        dalloc(&W.w32, sizeof(float2) * NB);
+        dalloc(&W.vcur, sizeof(double2) * NB);
+        W.v32 = true;
+    }
+    if (needZ && !W.z) {
+        dalloc(&W.Z, sizeof(double2) * NB * W.m);
+        W.z = true;
+    }
+    return W;
+}
+
+}  // namespace
+
+void gmres_many_free(GmresMany* w)
+{
+    if (!w) return;
+    w->release();
+    delete w;
+}
+
+int gmres_run_many(const Tree& t, OpsDev& d, const void* M, PrecManyFn prec, int B, const double* f, double* x, const gmres_opts& o,
+                   gmres_stats* st, cudaStream_t s)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const long N = t.N, NB = N * (long)B;
+    const int m = o.restart;
+    if (m < 1 || m > kMaxM) fail(DAFMM_EBADARG, "restart must be in 1..128");
+    if (B < 2 || B > kMB) fail(DAFMM_EBADARG, "several right-hand sides: 2..64");
+    const bool lowp = o.precision == DAFMM_MIXED;
+    const bool left = prec && o.side == DAFMM_PREC_LEFT;
+    const bool useZ = prec && !left;
+    if (!d.gm) d.gm = new GmresMany();
+    GmresMany& W = many_workspace(*d.gm, N, B, m, !lowp, lowp, useZ);
+    double2* X = (double2*)x;
+    const double2* F = (const double2*)f;
+    const unsigned nbl = (unsigned)((NB + kThreads - 1) / kThreads);
+    std::vector<double2> hb(B);
+    // squared column norms of a complex128 [N][B] block into out[0..B)
+    auto norms = [&](const double2* v, double2* out) {
+        many_dots_kernel<double><<<dim3(W.nrb, 1), kMT, 0, s>>>(N, B, v, 1, v, W.part);
+        many_reduce_kernel<<<1, kMT, 0, s>>>(W.nrb, B, W.part, out);
+    };
+    auto read_norms = [&](const double2* dev, std::vector<double>& out) {
+        CK(cudaMemcpyAsync(hb.data(), dev, sizeof(double2) * B, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int c = 0; c < B; c++) out[c] = std::sqrt(std::max(hb[c].x, 0.0));
+    };
+    auto upload = [&](int* dev, const std::vector<int>& h) {
+        CK(cudaMemcpyAsync(dev, h.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+    };
+    int matvecs = 0, applies = 0;
+    // one lockstep Arnoldi step for every column
+    auto enqueue_step = [&](int j) {
+        const double2* vj = lowp ? W.vcur : W.V64 + (size_t)j * NB;
+        if (left) {
+            CK(cudaMemcpyAsync(W.zin, vj, sizeof(double2) * NB, cudaMemcpyDeviceToDevice, s));
+            apply_matvec(t, d, B, (const double*)W.zin, (double*)W.tv, o.precision, s);
+            matvecs++;
+            prec(M, B, (const double*)W.tv, (double*)W.w64, o.precision, s);
+            applies++;
+        } else {
+            if (useZ) {
+                double2* zj = W.Z + (size_t)j * NB;
+                prec(M, B, (const double*)vj, (double*)zj, o.precision, s);
+                applies++;
+                CK(cudaMemcpyAsync(W.zin, zj, sizeof(double2) * NB, cudaMemcpyDeviceToDevice, s));
+            } else {
+                CK(cudaMemcpyAsync(W.zin, vj, sizeof(double2) * NB, cudaMemcpyDeviceToDevice, s));
+            }
+            apply_matvec(t, d, B, (const double*)W.zin, (double*)W.w64, o.precision, s);
+            matvecs++;
+        }
+        const int nk = j + 1;
+        const dim3 gd(W.nrb, (nk + kMK - 1) / kMK);
+        double2* wn2 = W.sc + 2 * B;
+        if (lowp) {
+            many_update_kernel<float><<<nbl, kThreads, 0, s>>>(NB, B, W.V32, 0, nullptr, W.w32, W.w64);
+            many_dots_kernel<float><<<gd, kMT, 0, s>>>(N, B, W.V32, nk, W.w32, W.part);
+            many_reduce_kernel<<<nk, kMT, 0, s>>>(W.nrb, B, W.part, W.h1);
+            many_update_kernel<float><<<nbl, kThreads, 0, s>>>(NB, B, W.V32, nk, W.h1, W.w32, nullptr);
+            many_dots_kernel<float><<<gd, kMT, 0, s>>>(N, B, W.V32, nk, W.w32, W.part);
+            many_reduce_kernel<<<nk, kMT, 0, s>>>(W.nrb, B, W.part, W.h2);
+            many_update_kernel<float><<<nbl, kThreads, 0, s>>>(NB, B, W.V32, nk, W.h2, W.w32, nullptr);
+            many_dots_kernel<float><<<dim3(W.nrb, 1), kMT, 0, s>>>(N, B, W.w32, 1, W.w32, W.part);
+            many_reduce_kernel<<<1, kMT, 0, s>>>(W.nrb, B, W.part, wn2);
+            many_givens_kernel<<<1, kMB, 0, s>>>(j, m, B, W.h1, W.h2, wn2, W.H, W.cs, W.sn, W.g, W.res);
+            many_scale_kernel<float><<<nbl, kThreads, 0, s>>>(NB, B, W.w32, nullptr, wn2, W.active, W.V32 + (size_t)(j + 1) * NB, W.vcur);
+        } else {
+            many_dots_kernel<double><<<gd, kMT, 0, s>>>(N, B, W.V64, nk, W.w64, W.part);
+            many_reduce_kernel<<<nk, kMT, 0, s>>>(W.nrb, B, W.part, W.h1);
+            many_update_kernel<double><<<nbl, kThreads, 0, s>>>(NB, B, W.V64, nk, W.h1, W.w64, nullptr);
+            many_dots_kernel<double><<<gd, kMT, 0, s>>>(N, B, W.V64, nk, W.w64, W.part);
+            many_reduce_kernel<<<nk, kMT, 0, s>>>(W.nrb, B, W.part, W.h2);
+            many_update_kernel<double><<<nbl, kThreads, 0, s>>>(NB, B, W.V64, nk, W.h2, W.w64, nullptr);
+            many_dots_kernel<double><<<dim3(W.nrb, 1), kMT, 0, s>>>(N, B, W.w64, 1, W.w64, W.part);
+            many_reduce_kernel<<<1, kMT, 0, s>>>(W.nrb, B, W.part, wn2);
+            many_givens_kernel<<<1, kMB, 0, s>>>(j, m, B, W.h1, W.h2, wn2, W.H, W.cs, W.sn, W.g, W.res);
+            many_scale_kernel<double>
+                <<<nbl, kThreads, 0, s>>>(NB, B, W.w64, nullptr, wn2, W.active, W.V64 + (size_t)(j + 1) * NB, nullptr);
+        }
+        CK(cudaMemcpyAsync(W.res_host, W.res, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    };
+    std::vector<double> nf(B), rn(B), rn0(B), rel(B, 0.0), inner(B), xn(B);
+    std::vector<int> done(B, 0), stop(B, 0), act(B, 0), zf(B, 0), iters(B, 0), outers(B, 0);
+    norms(F, W.sc);
+    read_norms(W.sc, nf);
+    // a zero right-hand side has the zero solution
+    bool anyzero = false;
+    for (int c = 0; c < B; c++) {
+        zf[c] = nf[c] == 0.0;
+        anyzero |= zf[c] != 0;
+    }
+    if (anyzero) {
+        upload(W.flag, zf);
+        many_zero_cols_kernel<<<nbl, kThreads, 0, s>>>(NB, B, W.flag, X);
+    }
+    norms(X, W.sc + B);
+    read_norms(W.sc + B, xn);
+    bool x_zero = true;
+    for (int c = 0; c < B; c++) x_zero &= xn[c] == 0.0;
+    int total = 0;
+    bool all = false;
+    for (int outer = 0;; outer++) {
+        // true residuals in FP64: r = f - A x (a zero initial guess needs no application)
+        if (x_zero) {
+            CK(cudaMemcpyAsync(W.r, F, sizeof(double2) * NB, cudaMemcpyDeviceToDevice, s));
+            x_zero = false;
+        } else {
+            apply_matvec(t, d, B, (const double*)X, (double*)W.tv, DAFMM_FP64, s);
+            matvecs++;
+            sub_kernel<<<nbl, kThreads, 0, s>>>(NB, F, W.tv, W.r);
+        }
+        norms(W.r, W.sc);
+        read_norms(W.sc, rn);
+        all = true;
+        double worst = 0;
+        for (int c = 0; c < B; c++) {
+            rel[c] = nf[c] > 0 ? rn[c] / nf[c] : 0.0;
+            if (!done[c]) outers[c] = outer;
+            done[c] = rel[c] <= o.tol;
+            all &= done[c] != 0;
+            worst = std::max(worst, rel[c]);
+        }
+        if (o.history && total < o.history_len) o.history[total] = worst;
+        if (all || total >= o.max_iters) break;
+        // one flexible GMRES cycle per unfinished column on A d = r (left: M^{-1} A d = M^{-1} r)
+        for (int c = 0; c < B; c++) {
+            act[c] = !done[c];
+            inner[c] = lowp ? std::max(o.inner_tol, o.tol / rel[c] * 0.5) : o.tol / rel[c] * 0.5;
+        }
+        upload(W.active, act);
+        const double2* r0 = W.r;
+        double2* r0n2 = W.sc;
+        rn0 = rn;
+        if (left) {
+            prec(M, B, (const double*)W.r, (double*)W.tv, o.precision, s);
+            applies++;
+            norms(W.tv, W.sc + B);
+            read_norms(W.sc + B, rn0);
+            r0 = W.tv;
+            r0n2 = W.sc + B;
+        }
+        if (lowp)
+            many_scale_kernel<float><<<nbl, kThreads, 0, s>>>(NB, B, nullptr, r0, r0n2, W.active, W.V32, W.vcur);
+        else
+            many_scale_kernel<double><<<nbl, kThreads, 0, s>>>(NB, B, nullptr, r0, r0n2, W.active, W.V64, nullptr);
+        many_init_g_kernel<<<(B * (m + 1) + 127) / 128, 128, 0, s>>>(m, B, r0n2, W.active, W.g);
+        const int steps = std::min(m, o.max_iters - total);
+        for (int c = 0; c < B; c++) stop[c] = act[c] ? -1 : 0;
+        for (int j = 0;; j++) {
+            enqueue_step(j);
+            CK(cudaStreamSynchronize(s));
+            total++;
+            bool running = false;
+            double mx = 0;
+            for (int c = 0; c < B; c++) {
+                if (stop[c] >= 0) continue;
+                const double est = rn0[c] > 0 ? W.res_host[c] / rn0[c] : 0.0;
+                mx = std::max(mx, est * rel[c]);
+                if (est <= inner[c])
+                    stop[c] = j + 1;
+                else
+                    running = true;
+            }
+            if (o.history && total < o.history_len) o.history[total] = mx;
+            if (!running) break;
+            if (j + 1 >= steps) {
+                for (int c = 0; c < B; c++)
+                    if (stop[c] < 0) stop[c] = j + 1;
+                break;
+            }
+        }
+        for (int c = 0; c < B; c++) iters[c] += stop[c];
+        upload(W.nstop, stop);
+        many_backsolve_kernel<<<B, kMaxM, 0, s>>>(m, W.nstop, W.H, W.g, W.y);
+        if (useZ)
+            many_add_zy_kernel<double2><<<nbl, kThreads, 0, s>>>(NB, B, m, W.Z, W.nstop, W.y, X);
+        else if (lowp)
+            many_add_zy_kernel<float2><<<nbl, kThreads, 0, s>>>(NB, B, m, W.V32, W.nstop, W.y, X);
+        else
+            many_add_zy_kernel<double2><<<nbl, kThreads, 0, s>>>(NB, B, m, W.V64, W.nstop, W.y, X);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(s));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int c = 0; c < B; c++) {
+        std::memset(&st[c], 0, sizeof(gmres_stats));
+        st[c].iterations = iters[c];
+        st[c].outer_iterations = outers[c];
+        st[c].matvecs = matvecs;
+        st[c].precond_applies = applies;
+        st[c].converged = done[c];
+        st[c].rel_residual = rel[c];
+        st[c].seconds = secs;
+    }
+    return all ? DAFMM_OK : DAFMM_ENOTCONV;
 }
 
 }  // namespace dafmm

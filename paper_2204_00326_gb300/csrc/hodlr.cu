@@ -119,6 +119,12 @@ struct dafmm_hodlr {
     mutable int stall = 0;    // test support: the next apply waits for one CTA too many
     int rmax = 0;
     double seconds = 0;
+    // several right-hand sides (hodlr_solve with nrhs > 1), grown on demand:
+    // work vector [N][nrhs], segment partials [segment][q][nrhs], s per node [node][2 r][nrhs]
+    void* bx = nullptr;
+    void* bpart = nullptr;
+    void* bs = nullptr;
+    int bcap = 0;  // right-hand sides the buffers hold
 };
 
 namespace dafmm {
@@ -718,9 +724,295 @@ int apply_ctas(const dafmm_hodlr& h)
     return (int)c;
 }
 
+
+// ------------------------------------------------------------------------
+// Several right-hand sides: x = A~^{-1} b for up to 64 columns stored
+// [N][nrhs] (right-hand side fastest).  The steps of the single-column
+// launch, as ordinary launches per level (at many columns every step has
+// work for the whole GPU, so no grid barrier is needed): the leaf inverses;
+// then per level from the leaves up the segment partials of t = W x, the
+// node's t and s = S^{-1} t, and x -= Ut s.  Threads take consecutive
+// columns, so a vector row is one coalesced access; the factor entries a
+// CTA needs and the vector rows it reads are staged in shared memory.  Sums
+// run in a fixed order (results do not depend on timing).
+
+constexpr int kBT = 256;     // threads of the several-column kernels
+constexpr int kBC = 64;      // columns one CTA covers (nrhs <= 64)
+constexpr int kBRows = 64;   // vector rows staged at a time
+constexpr int kBQ = 32;      // factor rows staged at a time
+constexpr int kBSCols = 16;  // columns per CTA of the s step
+constexpr int kBMaxRank = 256;
+
+// x[leaf rows][c] = inv_leaf b[leaf rows][c]; one CTA per leaf.
+template <typename T>
+__global__ void __launch_bounds__(kBT) hodlr_leaf_many_kernel(int lf, int B, const typename C2<T>::t* __restrict__ inv,
+                                                              const double2* __restrict__ b, typename C2<T>::t* __restrict__ x)
+{
+    using C = typename C2<T>::t;
+    using P = Ar<T>;
+    using A = typename P::A;
+    extern __shared__ __align__(16) unsigned char bsm[];
+    C* xs = (C*)bsm;          // rows x B: source rows j0 ..
+    C* ms = xs + kBRows * B;  // rows x kBRows: inv[j0 + j][i0 + i] (leaf inverses are column-major)
+    const int tid = threadIdx.x, c = tid % kBC, ig = tid / kBC;
+    const long l0 = (long)blockIdx.x * lf;
+    const C* M = inv + (size_t)blockIdx.x * lf * lf;
+    const int rows = min(lf, kBRows);
+    for (int i0 = 0; i0 < lf; i0 += rows) {
+        A acc[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) acc[k] = P::zero();
+        for (int j0 = 0; j0 < lf; j0 += rows) {
+            __syncthreads();
+            for (int e = tid; e < rows * B; e += kBT) xs[e] = P::from64(b[(l0 + j0) * B + e]);
+            for (int e = tid; e < rows * rows; e += kBT) {
+                const int j = e / rows, i = e - j * rows;
+                ms[j * kBRows + i] = M[(size_t)(j0 + j) * lf + i0 + i];
+            }
+            __syncthreads();
+            if (c < B)
+                for (int j = 0; j < rows; j++) {
+                    const C v = xs[j * B + c];
+#pragma unroll
+                    for (int k = 0; k < 16; k++)
+                        if (ig + 4 * k < rows) P::mac(acc[k], ms[j * kBRows + ig + 4 * k], v);
+                }
+        }
+        if (c < B)
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                if (ig + 4 * k < rows) x[(l0 + i0 + ig + 4 * k) * B + c] = P::to_c(acc[k]);
+    }
+}
+
+// part[g][q][c] = sum over the seg rows i of segment g of R[q][i] x[i][c]; one CTA per segment.
+template <typename T>
+__global__ void __launch_bounds__(kBT) hodlr_wx_many_kernel(long N, int B, int r, long seg, const typename C2<T>::t* __restrict__ R,
+                                                            const typename C2<T>::t* __restrict__ x, typename C2<T>::t* __restrict__ part)
+{
+    using C = typename C2<T>::t;
+    using P = Ar<T>;
+    using A = typename P::A;
+    extern __shared__ __align__(16) unsigned char bsm[];
+    C* xs = (C*)bsm;          // rows x B
+    C* rs = xs + kBRows * B;  // kBQ x kBRows: R[q0 + q][i0 + i]
+    const int tid = threadIdx.x, c = tid % kBC, qg = tid / kBC;
+    const long s0 = (long)blockIdx.x * seg;
+    const int rows = (int)min(seg, (long)kBRows);
+    for (int q0 = 0; q0 < r; q0 += kBQ) {
+        const int qn = min(kBQ, r - q0);
+        A acc[kBQ / 4];
+#pragma unroll
+        for (int k = 0; k < kBQ / 4; k++) acc[k] = P::zero();
+        for (long i0 = s0; i0 < s0 + seg; i0 += rows) {
+            __syncthreads();
+            for (int e = tid; e < rows * B; e += kBT) xs[e] = x[i0 * B + e];
+            for (int e = tid; e < qn * rows; e += kBT) {
+                const int q = e / rows, i = e - q * rows;
+                rs[q * kBRows + i] = R[(size_t)(q0 + q) * N + i0 + i];
+            }
+            __syncthreads();
+            if (c < B)
+                for (int i = 0; i < rows; i++) {
+                    const C v = xs[i * B + c];
+#pragma unroll
+                    for (int k = 0; k < kBQ / 4; k++)
+                        if (qg + 4 * k < qn) P::mac(acc[k], rs[(qg + 4 * k) * kBRows + i], v);
+                }
+        }
+        if (c < B)
+#pragma unroll
+            for (int k = 0; k < kBQ / 4; k++)
+                if (qg + 4 * k < qn) part[((size_t)blockIdx.x * r + q0 + qg + 4 * k) * B + c] = P::to_c(acc[k]);
+    }
+}
+
+// Node blockIdx.x, columns blockIdx.y * 16 ..: t (rows [0, r) from the partials of
+// half 2's segments, rows [r, 2r) from half 1's, summed in segment order), then
+// s = S^{-1} t into sout[node][2 r][c].
+template <typename T>
+__global__ void __launch_bounds__(kBT) hodlr_s_many_kernel(int B, int r, long gper, const typename C2<T>::t* __restrict__ part,
+                                                           const typename C2<T>::t* __restrict__ S, typename C2<T>::t* __restrict__ sout)
+{
+    using C = typename C2<T>::t;
+    using P = Ar<T>;
+    using A = typename P::A;
+    extern __shared__ __align__(16) unsigned char bsm[];
+    C* ts = (C*)bsm;  // 2 r x kBSCols
+    const int tid = threadIdx.x, cl = tid % kBSCols, ag = tid / kBSCols;
+    constexpr int kG = kBT / kBSCols;
+    const int c = blockIdx.y * kBSCols + cl;
+    const long nd = blockIdx.x;
+    const int R2 = 2 * r;
+    for (int a = ag; a < R2; a += kG) {
+        A acc = P::zero();
+        if (c < B) {
+            const long g0 = nd * 2 * gper + (a < r ? gper : 0);
+            const int q = a < r ? a : a - r;
+            for (long g = 0; g < gper; g++) P::add_c(acc, part[((g0 + g) * r + q) * B + c]);
+        }
+        ts[a * kBSCols + cl] = P::to_c(acc);
+    }
+    __syncthreads();
+    const C* Sn = S + (size_t)nd * 4 * r * r;
+    for (int a = ag; a < R2; a += kG) {
+        A acc = P::zero();
+        for (int bb = 0; bb < R2; bb++) P::mac(acc, Sn[(size_t)a * R2 + bb], ts[bb * kBSCols + cl]);
+        if (c < B) sout[((size_t)nd * R2 + a) * B + c] = P::to_c(acc);
+    }
+}
+
+// x[i][c] -= sum_q Ut[q][i] s[node][hoff + q][c] on the tile of blockIdx.x
+// (tile rows, inside one half of one node).
+template <typename T>
+__global__ void __launch_bounds__(kBT) hodlr_upd_many_kernel(long N, int B, int r, long n, int tile, const typename C2<T>::t* __restrict__ U,
+                                                             const typename C2<T>::t* __restrict__ sbuf, typename C2<T>::t* __restrict__ x)
+{
+    using C = typename C2<T>::t;
+    using P = Ar<T>;
+    using A = typename P::A;
+    extern __shared__ __align__(16) unsigned char bsm[];
+    C* ss = (C*)bsm;        // kBQ x B
+    C* us = ss + kBQ * B;   // kBQ x kBRows
+    const int tid = threadIdx.x, c = tid % kBC, ig = tid / kBC;
+    const long i0 = (long)blockIdx.x * tile;
+    const long nd = i0 / n;
+    const int hoff = (i0 - nd * n) >= n / 2 ? r : 0;
+    const C* sn = sbuf + ((size_t)nd * 2 * r + hoff) * B;
+    A acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc[k] = P::zero();
+    for (int q0 = 0; q0 < r; q0 += kBQ) {
+        const int qn = min(kBQ, r - q0);
+        __syncthreads();
+        for (int e = tid; e < qn * B; e += kBT) ss[e] = sn[(size_t)q0 * B + e];
+        for (int e = tid; e < qn * tile; e += kBT) {
+            const int q = e / tile, i = e - q * tile;
+            us[q * kBRows + i] = U[(size_t)(q0 + q) * N + i0 + i];
+        }
+        __syncthreads();
+        if (c < B)
+            for (int q = 0; q < qn; q++) {
+                const C sv = ss[q * B + c];
+#pragma unroll
+                for (int k = 0; k < 16; k++)
+                    if (ig + 4 * k < tile) P::mac(acc[k], us[q * kBRows + ig + 4 * k], sv);
+            }
+    }
+    if (c < B)
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (ig + 4 * k < tile) {
+                C* xp = x + (i0 + ig + 4 * k) * B + c;
+                *xp = P::sub(*xp, acc[k]);
+            }
+}
+
+template <typename T>
+__global__ void hodlr_out_many_kernel(long n, const typename C2<T>::t* __restrict__ x, double2* __restrict__ out)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e < n) out[e] = Ar<T>::to64(x[e]);
+}
+
+// Segment length of level l for the several-column partials: the half, capped
+// so that a level has at least about 256 segments (one CTA each).
+long many_seg(const dafmm_hodlr& h, int l)
+{
+    const long half = (h.N >> l) / 2;
+    return std::min(half, std::max(64L, h.N / 256));
+}
+
+template <typename T>
+size_t many_smem(int kind, int B)
+{
+    using C = typename C2<T>::t;
+    switch (kind) {
+        case 0: return sizeof(C) * (size_t)(kBRows * B + kBRows * kBRows);  // leaf
+        case 1: return sizeof(C) * (size_t)(kBRows * B + kBQ * kBRows);     // W x
+        case 2: return sizeof(C) * (size_t)(2 * kBMaxRank * kBSCols);       // s
+        default: return sizeof(C) * (size_t)(kBQ * B + kBQ * kBRows);       // update
+    }
+}
+
+void ensure_many(dafmm_hodlr& h, int B)
+{
+    if (h.bcap >= B) return;
+    cudaFree(h.bx);
+    cudaFree(h.bpart);
+    cudaFree(h.bs);
+    h.bx = h.bpart = h.bs = nullptr;
+    h.bcap = 0;
+    size_t npart = 1, ns = 1;
+    for (int l = 0; l < h.H; l++) {
+        const int r = h.dlv[l].r;
+        npart = std::max(npart, (size_t)(h.N / many_seg(h, l)) * r);
+        ns = std::max(ns, (size_t)(1L << l) * 2 * r);
+    }
+    if (cudaMalloc(&h.bx, sizeof(double2) * (size_t)h.N * B) != cudaSuccess ||
+        cudaMalloc(&h.bpart, sizeof(double2) * npart * B) != cudaSuccess || cudaMalloc(&h.bs, sizeof(double2) * ns * B) != cudaSuccess) {
+        cudaGetLastError();
+        fail(DAFMM_ENOMEM, "device allocation for the several-right-hand-side HODLR buffers failed");
+    }
+    h.bcap = B;
+    static bool attrs = false;
+    if (!attrs) {
+        CK(cudaFuncSetAttribute(hodlr_leaf_many_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<double>(0, kBC)));
+        CK(cudaFuncSetAttribute(hodlr_leaf_many_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<float>(0, kBC)));
+        CK(cudaFuncSetAttribute(hodlr_wx_many_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<double>(1, kBC)));
+        CK(cudaFuncSetAttribute(hodlr_wx_many_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<float>(1, kBC)));
+        CK(cudaFuncSetAttribute(hodlr_s_many_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<double>(2, kBC)));
+        CK(cudaFuncSetAttribute(hodlr_s_many_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<float>(2, kBC)));
+        CK(cudaFuncSetAttribute(hodlr_upd_many_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<double>(3, kBC)));
+        CK(cudaFuncSetAttribute(hodlr_upd_many_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<float>(3, kBC)));
+        attrs = true;
+    }
+}
+
+template <typename T>
+void apply_many(dafmm_hodlr& h, int B, const double2* b, double2* xout, cudaStream_t s)
+{
+    using C = typename C2<T>::t;
+    ensure_many(h, B);
+    C* x = (C*)h.bx;
+    C* part = (C*)h.bpart;
+    C* sb = (C*)h.bs;
+    const C* inv = (const C*)(sizeof(T) == 8 ? (const void*)h.inv64 : (const void*)h.inv32);
+    hodlr_leaf_many_kernel<T><<<(unsigned)(h.N / h.leaf), kBT, many_smem<T>(0, B), s>>>(h.leaf, B, inv, b, x);
+    for (int l = h.H - 1; l >= 0; l--) {
+        const HodlrDevLevel& L = h.dlv[l];
+        const int r = L.r;
+        if (r == 0) continue;
+        const long n = h.N >> l, half = n / 2, seg = many_seg(h, l);
+        const C* R = (const C*)(sizeof(T) == 8 ? (const void*)L.R64 : (const void*)L.R32);
+        const C* U = (const C*)(sizeof(T) == 8 ? (const void*)L.Ut64 : (const void*)L.Ut32);
+        const C* S = (const C*)(sizeof(T) == 8 ? (const void*)L.S64 : (const void*)L.S32);
+        hodlr_wx_many_kernel<T><<<(unsigned)(h.N / seg), kBT, many_smem<T>(1, B), s>>>(h.N, B, r, seg, R, x, part);
+        hodlr_s_many_kernel<T><<<dim3((unsigned)(h.N / n), (unsigned)((B + kBSCols - 1) / kBSCols)), kBT, sizeof(C) * 2 * r * kBSCols, s>>>(
+            B, r, half / seg, part, S, sb);
+        const int tile = (int)std::min<long>(kBRows, half);
+        hodlr_upd_many_kernel<T><<<(unsigned)(h.N / tile), kBT, many_smem<T>(3, B), s>>>(h.N, B, r, n, tile, U, sb, x);
+    }
+    const long ne = h.N * (long)B;
+    hodlr_out_many_kernel<T><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(ne, x, xout);
+}
+
 }  // namespace
 
 const dafmm_tree* hodlr_tree(const dafmm_hodlr* h) { return h->tree; }
+
+void hodlr_apply_many(const dafmm_hodlr* h, int nrhs, const double* b, double* x, int precision, cudaStream_t s)
+{
+    cudaGetLastError();
+    if (nrhs < 1 || nrhs > kBC) fail(DAFMM_EBADARG, "hodlr_solve takes 1 to 64 right-hand sides");
+    if (h->rmax > kBMaxRank) fail(DAFMM_EBADARG, "several right-hand sides need HODLR ranks of at most 256");
+    dafmm_hodlr& hm = const_cast<dafmm_hodlr&>(*h);  // work buffers only
+    if (precision == DAFMM_FP64)
+        apply_many<double>(hm, nrhs, (const double2*)b, (double2*)x, s);
+    else
+        apply_many<float>(hm, nrhs, (const double2*)b, (double2*)x, s);
+    CK(cudaGetLastError());
+}
 
 void hodlr_apply(const dafmm_hodlr* h, const double* b, double* x, int precision, cudaStream_t s)
 {
@@ -761,6 +1053,11 @@ void hodlr_set_width(dafmm_hodlr* h, int ctas)
 void hodlr_prec(const void* M, const double* v, double* z, int precision, cudaStream_t s)
 {
     hodlr_apply((const dafmm_hodlr*)M, v, z, precision, s);
+}
+
+void hodlr_prec_many(const void* M, int nrhs, const double* v, double* z, int precision, cudaStream_t s)
+{
+    hodlr_apply_many((const dafmm_hodlr*)M, nrhs, v, z, precision, s);
 }
 
 dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf)
@@ -934,6 +1231,9 @@ void hodlr_free(dafmm_hodlr* h)
     cudaFree(h->xw);
     cudaFree(h->bar);
     cudaFree(h->err);
+    cudaFree(h->bx);
+    cudaFree(h->bpart);
+    cudaFree(h->bs);
     delete h;
 }
 
@@ -961,6 +1261,7 @@ void hodlr_dense(const dafmm_hodlr* h, cd* out)
         const long n = N >> l, half = n / 2;
         for (long k = 0; k < N / n; k++) {
             const long i0 = k * n;
+#pragma omp parallel for schedule(static)
             for (long i = 0; i < half; i++)
                 for (long j = 0; j < half; j++) {
                     cd a12 = 0, a21 = 0;

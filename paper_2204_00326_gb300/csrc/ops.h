@@ -98,6 +98,8 @@ constexpr int kGraphSlots = 4;        // cached (v, out) pairs per precision
 
 struct GmresWork;  // GMRES workspace kept between solves (gmres.cu)
 void gmres_work_free(GmresWork* w);
+struct GmresMany;  // the same for several right-hand sides
+void gmres_many_free(GmresMany* w);
 
 struct OpsDev {
     std::vector<LevelDev> lv;
@@ -131,6 +133,7 @@ struct OpsDev {
     GraphCache gc[2][kGraphSlots];
     unsigned long long gc_clock = 0;
     GmresWork* gw = nullptr;
+    GmresMany* gm = nullptr;
 };
 
 // Allocate and upload; frees host block storage as it goes.
@@ -150,12 +153,19 @@ void apply_matvec_noalloc(const Tree& t, const OpsDev& d, const double* v, doubl
 using PrecFn = void (*)(const void* M, const double* v, double* z, int precision, cudaStream_t s);
 int gmres_run(const Tree& t, OpsDev& d, const void* M, PrecFn prec, const double* f, double* x, const gmres_opts& o, gmres_stats& st,
               cudaStream_t s);
+// nrhs in 2..64 columns [N][nrhs] in lockstep; prec: z = M^{-1} v for all columns, or nullptr; st: nrhs entries
+using PrecManyFn = void (*)(const void* M, int nrhs, const double* v, double* z, int precision, cudaStream_t s);
+int gmres_run_many(const Tree& t, OpsDev& d, const void* M, PrecManyFn prec, int nrhs, const double* f, double* x, const gmres_opts& o,
+                   gmres_stats* st, cudaStream_t s);
 
 // HODLR (hodlr.cu)
 dafmm_hodlr* hodlr_build(const dafmm_ops* ops, int rank, double tol, int leaf);
 void hodlr_free(dafmm_hodlr* h);
 void hodlr_apply(const dafmm_hodlr* h, const double* b, double* x, int precision, cudaStream_t s);
 void hodlr_prec(const void* M, const double* v, double* z, int precision, cudaStream_t s);
+// nrhs in 2..64 columns stored [N][nrhs]: per-level launches, no device waits
+void hodlr_apply_many(const dafmm_hodlr* h, int nrhs, const double* b, double* x, int precision, cudaStream_t s);
+void hodlr_prec_many(const void* M, int nrhs, const double* v, double* z, int precision, cudaStream_t s);
 // Synchronise s; DAFMM_ETIMEOUT (flag cleared, counters re-armed) when an apply gave up a wait.
 int hodlr_check(const dafmm_hodlr* h, cudaStream_t s);
 void hodlr_set_stall(const dafmm_hodlr* h, int on);

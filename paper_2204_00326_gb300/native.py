@@ -162,7 +162,7 @@ _sig = {
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_potential": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_set_contrast": ([_P, _P, _P], ctypes.c_int),
-    "gmres_solve": ([_P, _P, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
+    "gmres_solve": ([_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
     "hodlr_factor": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hodlr_solve": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "hodlr_sync": ([_P, _P], ctypes.c_int),
@@ -340,10 +340,16 @@ def gmres_solve(ops: int, f, x, tol: float = 1e-8, precision: int = DAFMM_FP64, 
                 inner_tol: float = 1e-5, M: int | None = None, stream=None, history_len: int = 0, side: int = 0):
     """Solve A x = f (x holds the initial guess on entry).  Returns (status, stats, history).
 
+    f and x are (N,) or (N, nrhs) complex128 (nrhs <= 64, right-hand side
+    fastest); with several right-hand sides the columns are solved together
+    (one batched application per step) and stats is a list of nrhs entries.
     side: DAFMM_PREC_RIGHT (0) or DAFMM_PREC_LEFT (1) preconditioning by M.
     status is DAFMM_OK or DAFMM_ENOTCONV (not converged within max_iters); other
     failures raise DafmmError.
     """
+    nrhs = 1 if f.dim() == 1 else f.shape[1]
+    if x.shape != f.shape:
+        raise ValueError("f and x must have the same shape")
     o = gmres_opts()
     o.side = side
     o.restart = restart
@@ -356,12 +362,13 @@ def gmres_solve(ops: int, f, x, tol: float = 1e-8, precision: int = DAFMM_FP64, 
         hist = (ctypes.c_double * history_len)()
         o.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
         o.history_len = history_len
-    st = gmres_stats()
-    rc = lib.gmres_solve(ops, M, _dptr(f, "complex128"), _dptr(x, "complex128"), ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
+    sts = (gmres_stats * nrhs)()
+    rc = lib.gmres_solve(ops, M, nrhs, _dptr(f, "complex128"), _dptr(x, "complex128"), ctypes.byref(o), sts, _stream_ptr(stream))
     if rc not in (DAFMM_OK, DAFMM_ENOTCONV):
         _check(rc)
-    h = list(hist)[: min(history_len, st.iterations + st.outer_iterations + 1)] if hist is not None else None
-    return rc, st, h
+    n_hist = max(s.iterations + s.outer_iterations + 1 for s in sts)
+    h = list(hist)[: min(history_len, n_hist)] if hist is not None else None
+    return rc, (sts[0] if nrhs == 1 else list(sts)), h
 
 
 def hodlr_factor(ops: int, rank: int = 15, tol: float = 0.0, leaf_size: int = 64) -> int:
@@ -371,7 +378,11 @@ def hodlr_factor(ops: int, rank: int = 15, tol: float = 0.0, leaf_size: int = 64
 
 
 def hodlr_solve(M: int, b, x, precision: int = DAFMM_FP64, stream=None) -> None:
-    _check(lib.hodlr_solve(M, 1, _dptr(b, "complex128"), _dptr(x, "complex128"), precision, _stream_ptr(stream)))
+    """x = A~^{-1} b for (N,) or (N, nrhs) complex128 (nrhs <= 64, right-hand side fastest)."""
+    nrhs = 1 if b.dim() == 1 else b.shape[1]
+    if x.shape != b.shape:
+        raise ValueError("b and x must have the same shape")
+    _check(lib.hodlr_solve(M, nrhs, _dptr(b, "complex128"), _dptr(x, "complex128"), precision, _stream_ptr(stream)))
 
 
 def hodlr_sync(M: int, stream=None) -> None:

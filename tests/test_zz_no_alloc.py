@@ -52,5 +52,52 @@ def test_noalloc_argument_errors():
 
     pkg.build()
     from paper_2204_00326_gb300 import native as N
+    from paper_2204_00326_gb300.operator import DafmmOperator
 
     assert N.lib.dafmm_matvec_noalloc(None, None, None, 0, None) == N.DAFMM_EBADARG
+    w = W.GRID32_K8
+    op = DafmmOperator(w.n_side, w.kappa, lambda xy: W.contrast(w, xy))
+    v = torch.as_tensor(W.random_vector(w.N, 1, seed=33)[:, 0], device="cuda")
+    out = torch.empty_like(v)
+    with pytest.raises(N.DafmmError) as e:  # unknown precision
+        N.dafmm_matvec_noalloc(op.ops, v, out, 7)
+    assert e.value.code == N.DAFMM_EBADARG
+    with pytest.raises(N.DafmmError) as e:  # input and output alias
+        N.dafmm_matvec_noalloc(op.ops, v, v, N.DAFMM_FP64)
+    assert e.value.code == N.DAFMM_EBADARG
+    op.close()
+
+
+def test_noalloc_rejects_problems_larger_than_its_scratch():
+    """A problem whose coefficients do not fit the static array is refused
+    with DAFMM_EBADARG before any work is queued, and the output is left as
+    it was.  Smaller problems on the way give the same result as
+    dafmm_matvec."""
+    import paper_2204_00326_gb300 as pkg
+
+    pkg.build()
+    from paper_2204_00326_gb300 import native as N
+    from paper_2204_00326_gb300.operator import DafmmOperator
+
+    rejected = None
+    for w in (W.GRID256_K80, W.GRID512_K160):
+        op = DafmmOperator(w.n_side, w.kappa, lambda xy: W.contrast(w, xy))
+        try:
+            v = torch.as_tensor(W.random_vector(w.N, 1, seed=34)[:, 0], device="cuda")
+            got = torch.full_like(v, complex(1.5, -2.5))
+            try:
+                N.dafmm_matvec_noalloc(op.ops, v, got, N.DAFMM_MIXED)
+            except N.DafmmError as e:
+                torch.cuda.synchronize()
+                assert e.code == N.DAFMM_EBADARG
+                assert str(N.NOALLOC_SCRATCH_BYTES) in str(e)
+                assert bool((got == complex(1.5, -2.5)).all())
+                rejected = w.name
+                break
+            ref = torch.empty_like(v)
+            N.dafmm_matvec(op.ops, v, ref, N.DAFMM_MIXED)
+            torch.cuda.synchronize()
+            assert _rel(got, ref) < MIXED_TOL
+        finally:
+            op.close()
+    assert rejected is not None

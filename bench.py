@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--eps-nca", type=float, default=1e-12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-residual solves")
+    ap.add_argument("--no-batched-solve", action="store_true",
+                    help="skip the 64-plane-wave solve on the 256 x 256, kappa = 80 disc workload")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides of the batched measurement (1 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--learned", action="store_true",
@@ -268,6 +270,52 @@ def run_learned(a):
     print(json.dumps(result), flush=True)
 
 
+def batched_solve(N, DafmmOperator, nrhs=64, rank=15, singles=4):
+    """Time to 1e-8 for nrhs plane waves (theta_k = 2 pi k / nrhs) solved
+    together on the 256 x 256, kappa = 80 disc workload: HODLR-preconditioned
+    GMRES (rank `rank`), one batched application and one batched HODLR apply
+    per step, FP64 and mixed precision with FP64 refinement.  A few columns
+    solved one at a time give the per-right-hand-side cost without batching."""
+    import torch
+
+    w = W.GRID256_K80
+    t0 = time.perf_counter()
+    op = DafmmOperator(w.n_side, w.kappa, lambda xy: W.contrast(w, xy))
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M = N.hodlr_factor(op.ops, rank=rank, leaf_size=64)
+    t_factor = time.perf_counter() - t0
+    F = torch.as_tensor(W.plane_waves(w.kappa, op.xy, nrhs) * (-w.kappa ** 2 * op.q)[:, None], device="cuda").contiguous()
+    out = {"workload": w.name, "N": w.N, "nrhs": nrhs, "tol": 1e-8, "hodlr_rank": rank, "setup_s": setup,
+           "hodlr_factor_s": t_factor, "setup_excluded": True}
+    for name, prec in (("fp64", N.DAFMM_FP64), ("mixed", N.DAFMM_MIXED)):
+        for rep in range(2):  # the first solve warms up (workspaces, graph capture)
+            X = torch.zeros_like(F)
+            rc, sts, _ = N.gmres_solve(op.ops, F, X, tol=1e-8, precision=prec, restart=50, max_iters=2000, M=M)
+        its = [s.iterations for s in sts]
+        out[name] = {"seconds": sts[0].seconds, "converged": all(s.converged for s in sts),
+                     "worst_rel_residual": max(s.rel_residual for s in sts), "steps": sts[0].matvecs,
+                     "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
+                     "munknowns_rhs_per_s": w.N * nrhs / sts[0].seconds / 1e6}
+    # the same columns one at a time (mixed), for the per-right-hand-side cost without batching
+    f1 = F[:, 0].contiguous()
+    x1 = torch.zeros_like(f1)
+    N.gmres_solve(op.ops, f1, x1, tol=1e-8, precision=N.DAFMM_MIXED, restart=50, max_iters=2000, M=M)
+    secs, its = [], []
+    for k in range(singles):
+        fk = F[:, k * (nrhs // singles)].contiguous()
+        xk = torch.zeros_like(fk)
+        rc, st, _ = N.gmres_solve(op.ops, fk, xk, tol=1e-8, precision=N.DAFMM_MIXED, restart=50, max_iters=2000, M=M)
+        secs.append(st.seconds)
+        its.append(st.iterations)
+    out["mixed_one_at_a_time"] = {"columns": singles, "seconds_per_rhs": float(np.mean(secs)), "iterations_mean": float(np.mean(its))}
+    out["mixed_batched_seconds_per_rhs"] = out["mixed"]["seconds"] / nrhs
+    out["mixed_vs_fp64_speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    N.hodlr_destroy(M)
+    op.close()
+    return out
+
+
 def main():
     a = _args()
     w = W.WORKLOADS[a.workload]
@@ -437,6 +485,10 @@ def main():
         N.hodlr_destroy(M)
         N.hodlr_destroy(Mt)
 
+    ttr_b = None
+    if not a.no_batched_solve and world == 1:
+        ttr_b = batched_solve(N, DafmmOperator)
+
     clk.__exit__(None, None, None)
 
     cpu = None
@@ -460,6 +512,7 @@ def main():
                  "gpu_launches": int(st.launches_per_call_fp64 * a.steps)},
         "batched": batched,
         "time_to_residual": ttr,
+        "time_to_residual_batched": ttr_b,
         "setup_s": {"total": setup_s, "entry_table": st.setup_seconds_table, "nca": st.setup_seconds_nca},
         "operator": {"bytes_fp32": st.operator_bytes_fp32, "bytes_fp64": st.operator_bytes_fp64,
                      "cmacs_per_rhs": st.cmacs_per_rhs},

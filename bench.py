@@ -79,6 +79,15 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    """Dense bf16 TFLOP/s (burst): measured, else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f).get("bf16_tflops", 1900.0), "measured"
+    return 1900.0, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
@@ -458,6 +467,29 @@ def main():
                              "ms_per_step": msb}
         cm = st.cmacs_per_rhs * a.nrhs
         batched["mixed"]["achieved_tflops"] = 8.0 * cm / (batched["mixed"]["ms_per_step"] * 1e-3) / 1e12
+        # the same application with the tree passes on the tensor cores (opt-in kernel)
+        N.dafmm_set_batched_kernel(op.ops, N.BATCHED_TENSOR_CORES)
+        for _ in range(a.warmup):
+            flush.zero_()
+            op.matvec(Vb, Yb, N.DAFMM_MIXED)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for e0b, e1b in evs:
+            flush.zero_()
+            e0b.record(stream)
+            op.matvec(Vb, Yb, N.DAFMM_MIXED)
+            e1b.record(stream)
+        torch.cuda.synchronize()
+        N.dafmm_set_batched_kernel(op.ops, N.BATCHED_AUTO)
+        mst = sum(x.elapsed_time(y) for x, y in evs) / a.steps
+        cm_tree = (st.cmacs_up + st.cmacs_m2l + st.cmacs_down) * a.nrhs
+        issued = 64.0 * cm_tree  # tensor flops issued per complex MAC: 8 (real embedding) x 2 (stacked rows) x 4 (MMAs)
+        batched["mixed_tensor_cores"] = {
+            "value": w.N * a.nrhs / (mst * 1e-3) / 1e6, "unit": "Munknowns/s (unknowns x rhs)", "ms_per_step": mst,
+            "kernel": "stream_batched_tc_kernel: tcgen05.mma kind::tf32, three-part tf32 split, per-chunk accumulators",
+            "issued_tensor_tflops_upper_bound": issued / (mst * 1e-3) / 1e12,
+            "bf16_peak_tflops": _bf16_peak()[0], "peak_kind": _bf16_peak()[1] + " bf16 (tf32 runs at half the bf16 rate)",
+            "note": "not the default: slower than the CUDA-core kernel at these chunk shapes"}
         del Vb, Yb
 
     # time to relative residual 1e-8 (FP64 residual), f = -kappa^2 q u_inc

@@ -415,6 +415,20 @@ int dafmm_set_contrast(dafmm_ops* ops, const double* q_dev, void* stream);
  */
 int dafmm_debug_stall(dafmm_ops* ops, int pass);
 
+/*
+ * dafmm_set_batched_kernel -- which kernel runs the tree passes (P2M, M2M,
+ * M2L, L2L) of a complex64 (DAFMM_MIXED) application with several
+ * right-hand sides: 0 automatic (currently the CUDA cores: faster at the
+ * chunk shapes of these operators), 1 CUDA cores (FP32 FMA), 2 tensor cores.
+ * The tensor-core kernel computes each block product as a real GEMM on
+ * tcgen05.mma (kind::tf32) with every FP32 value split exactly into three
+ * tf32 parts, and drains each chunk's accumulator into FP32 registers;
+ * results differ from the CUDA-core kernel by FP32 rounding only.  Complex128 applications and single right-hand sides are
+ * not affected.  Cached application graphs are dropped when the mode
+ * changes.  Errors: DAFMM_EBADARG for a NULL handle or a mode outside 0..2.
+ */
+int dafmm_set_batched_kernel(dafmm_ops* ops, int mode);
+
 /* Realised ranks, operator bytes and work of one application. */
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats);
 

@@ -1292,6 +1292,350 @@ __global__ void __launch_bounds__(128) stream_batched_kernel(int nch, int kpc, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Several right-hand sides on the tensor cores (complex64 operators).  A
+// chunk's product Y[i][r] += sum_k M[i][k] X[k][r] (i < ro rows, k < ncol
+// columns, r < nrhs <= 64) is a real GEMM after the usual embedding of
+// complex numbers: with a K index 2k + t (t = 0 real part, 1 imaginary part
+// of X[k][r]) the 2 NR output columns are [Re Y_0 .. Re Y_{ro-1} | pad |
+// Im Y_0 ..] and B[i][2k] = Re M, B[i][2k+1] = -Im M, B[NR+i][2k] = Im M,
+// B[NR+i][2k+1] = Re M.  tcgen05.mma kind::tf32 (D in TMEM, FP32) multiplies
+// 11-bit significands, so every FP32 value v is split exactly into three
+// tf32 parts v = h + m + l (h = rn(v), m = rn(v - h), l = v - h - m).  A
+// holds X_h in rows 0..63 and X_m in rows 64..127 (M = 128) and A2 holds X_l
+// over zeros; per K step D += A B_h + A B_m + A B_l + A2 B_h, so D rows r and
+// 64 + r together hold every partial product down to 2^-33 relative (terms
+// below are dropped), i.e. the FP32 products of the CUDA-core kernel.  The
+// tensor core's own FP32 accumulation over a long chain of MMAs loses more
+// than rounded FMAs do (measured: five times the CUDA-core kernel's error
+// when a row's whole chain accumulated in TMEM), so each chunk's MMAs start a
+// fresh accumulator (at most 32 MMAs deep) that is drained into FP32
+// registers with rounded additions (tcgen05.ld) before the next chunk's
+// MMAs.  Operands are K-major 8 x 16-byte core matrices without swizzle.
+constexpr int kTcThreads = 256;
+constexpr int kTcRaw = 3;              // bulk-copy stages of raw chunks
+constexpr int kTcA = 128 * 64 * 4;     // A (and A2) operand: 128 rows x 64 K (tf32)
+constexpr int kTcBPart = 5120 * 4;     // one tf32 part of B for the largest chunk shape (2 NR x Kpad <= 5120)
+constexpr int kTcB = 3 * kTcBPart;
+constexpr int kTcCols = 128;           // TMEM columns (N = 2 NR <= 128)
+
+__host__ __device__ inline int tc_raw_bytes(int nrhs_pad) { return BatchCfg<float>::stage_bytes(nrhs_pad); }
+__host__ __device__ inline int tc_smem_bytes(int nrhs_pad) { return kTcRaw * tc_raw_bytes(nrhs_pad) + 2 * kTcA + kTcB + 128; }
+
+// Byte offset of element (row, k) of a K-major operand with Kt columns: core
+// matrix (row / 8, k / 4) at 128 bytes each, row-group major.
+__device__ __forceinline__ unsigned tc_off(int row, int k, int Kt)
+{
+    return (unsigned)((((row >> 3) * (Kt >> 2) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (between core matrices along K), stride byte offset (between
+// 8-row groups), descriptor version 1, no swizzle.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ float tc_rn(float v)
+{
+    unsigned h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+    return __uint_as_float(h);
+}
+
+// v = h + m + l exactly, each a tf32 value.
+__device__ __forceinline__ void tc_split3(float v, float& h, float& m, float& l)
+{
+    h = tc_rn(v);
+    const float r = v - h;  // exact
+    m = tc_rn(r);
+    l = tc_rn(r - m);       // exact: at most two significant bits remain
+}
+
+// Chunk in raw stage (matrix M, ld x ncol column-major; inputs xs[k][r]) ->
+// operands A, A2 (128 x Kpad) and the three parts of B (N x Kpad).  Rows of B
+// past ro and rows of A, A2 past nrhs only reach accumulator rows or columns
+// the epilogue never reads, except the rows 64..64+nrhs of A2, which are
+// zeroed.  The K padding is zero in every operand.
+__device__ __forceinline__ void tc_convert(const float2* M, int ld, int ro, int NR, int ncol, int Kpad, const float2* xs, int nrhs_pad,
+                                           int nrhs, unsigned char* A, unsigned char* A2, unsigned char* B, int tid)
+{
+    for (int e = tid; e < ro * ncol; e += kTcThreads) {
+        const int k = e / ro, i = e - k * ro;
+        const float2 mv = M[k * ld + i];
+        float r[3], im[3];
+        tc_split3(mv.x, r[0], r[1], r[2]);
+        tc_split3(mv.y, im[0], im[1], im[2]);
+        const unsigned o1 = tc_off(i, 2 * k, Kpad), o2 = tc_off(NR + i, 2 * k, Kpad);
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+            *(float2*)(B + p * kTcBPart + o1) = make_float2(r[p], -im[p]);
+            *(float2*)(B + p * kTcBPart + o2) = make_float2(im[p], r[p]);
+        }
+    }
+    for (int e = tid; e < ncol * 64; e += kTcThreads) {
+        const int k = e >> 6, r = e & 63;
+        if (r < nrhs) {
+            const float2 x = xs[k * nrhs_pad + r];
+            float a[3], b[3];
+            tc_split3(x.x, a[0], a[1], a[2]);
+            tc_split3(x.y, b[0], b[1], b[2]);
+            *(float2*)(A + tc_off(r, 2 * k, Kpad)) = make_float2(a[0], b[0]);
+            *(float2*)(A + tc_off(64 + r, 2 * k, Kpad)) = make_float2(a[1], b[1]);
+            *(float2*)(A2 + tc_off(r, 2 * k, Kpad)) = make_float2(a[2], b[2]);
+            *(float2*)(A2 + tc_off(64 + r, 2 * k, Kpad)) = make_float2(0.f, 0.f);
+        }
+    }
+    const int kp = Kpad - 2 * ncol;  // zero K padding (0, 2, 4 or 6 columns)
+    if (kp > 0) {
+        const int N = 2 * NR;
+        for (int e = tid; e < (128 + N) * kp; e += kTcThreads) {
+            const int row = e / kp, k = 2 * ncol + (e - row * kp);
+            if (row < 128) {
+                *(float*)(A + tc_off(row, k, Kpad)) = 0.f;
+                *(float*)(A2 + tc_off(row, k, Kpad)) = 0.f;
+            } else {
+#pragma unroll
+                for (int p = 0; p < 3; p++) *(float*)(B + p * kTcBPart + tc_off(row - 128, k, Kpad)) = 0.f;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// One tcgen05.mma (kind::tf32, one CTA): D (+)= A B^T with the given descriptors.
+__device__ __forceinline__ void tc_mma(unsigned tmem, unsigned long long ad, unsigned long long bd, unsigned idesc, unsigned acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 8 consecutive accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tc_ld8(unsigned taddr, float (&v)[8])
+{
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = __uint_as_float(r[j]);
+}
+
+// The several-right-hand-side pass on the tensor cores: the chunk ranges and
+// split-row handling of stream_batched_kernel with a three-stage bulk-copy
+// pipeline of raw chunks.  Per chunk: wait for its raw stage and for the
+// previous chunk's MMAs (one operand set), convert, one thread issues the
+// MMAs and commits them to the MMA barrier; at the end of a row the
+// accumulator goes through shared memory to the row's output.  Every wait is
+// bounded; on a timeout the CTA raises the device flag, waits (bounded) for
+// its copies and MMAs, frees its TMEM and returns.
+__global__ void __launch_bounds__(kTcThreads, 1) stream_batched_tc_kernel(int nch, int kpc, int nrhs, int nrhs_pad, int bulk_x,
+                                                                          const int4* __restrict__ recs,
+                                                                          const __grid_constant__ GroupArgs<float> g, float2* __restrict__ P,
+                                                                          int Pld, int* __restrict__ cnt, int* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_last;
+    __shared__ int s_bad;
+    __shared__ unsigned s_tmem;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cb = blockIdx.x * kpc;
+    const int ce = min(nch, cb + kpc);
+    if (cb >= ce) return;
+    const int rb = tc_raw_bytes(nrhs_pad);
+    auto raw = [&](int k) { return smem + k * rb; };
+    unsigned char* A = smem + kTcRaw * rb;
+    unsigned char* A2 = A + kTcA;
+    unsigned char* B = A2 + kTcA;
+    float* E = (float*)A;  // epilogue: accumulator columns x 128 lanes (overlays A and A2)
+    unsigned long long* bar = (unsigned long long*)(B + kTcB);  // [0, kTcRaw) raw stages, [kTcRaw] MMAs
+    unsigned long long* mbar = bar + kTcRaw;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)), "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int k = 0; k <= kTcRaw; k++) mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_bad = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = s_tmem;
+    int pend[kTcRaw];  // per raw stage: parity of a copy issued and not yet waited for
+#pragma unroll
+    for (int k = 0; k < kTcRaw; k++) {
+        pend[k] = -1;
+        if (cb + k < ce) {
+            batch_issue<float>(g, recs, cb + k, raw(k), &bar[k], nrhs, nrhs_pad, bulk_x, tid, kTcThreads);
+            pend[k] = 0;
+        }
+    }
+    int pslot = cb;
+    int issued = 0;        // chunks whose MMAs were committed
+    bool undrained = false;  // the previous chunk's accumulator is still in TMEM
+    int prevN = 0;           // its column count
+    // this thread's share of the row's accumulator: TMEM lane 32 (warp & 3) +
+    // lane, columns (warp >> 2) N/2 + j
+    float acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; j++) acc[j] = 0.f;
+    auto drain = [&](int N) {
+        const int q = warp & 3, half = N >> 1, col0 = (warp >> 2) * half;
+#pragma unroll
+        for (int g8 = 0; g8 < 8; g8++)
+            if (8 * g8 < half) {
+                float v[8];
+                tc_ld8(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(col0 + 8 * g8), v);
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[8 * g8 + j] += v[j];
+            }
+    };
+    for (int c = cb, it = 0; c < ce; c++, it++) {
+        const int s = it % kTcRaw;
+        const int4 ra = recs[2 * c];
+        const PassArgs<float>& pa = g.p[ra.x & 0xff];
+        const int ro = (ra.x >> 16) & 0xffff;
+        const int ld = ro + (ro & 1);
+        const int ncol = ra.z;
+        const int NR = (ro + 7) & ~7;
+        const int Kpad = 2 * ((ncol + 3) & ~3);
+        float2* xs = (float2*)(raw(s) + BatchCfg<float>::kMat);
+        if (!bulk_x)
+            for (int q = tid; q < ncol * nrhs; q += kTcThreads) {
+                const int k = q / nrhs, rr = q - k * nrhs;
+                xs[k * nrhs_pad + rr] = pa.x[(size_t)pa.xmap[ra.w + k] * nrhs + rr];
+            }
+        bool ok = mbar_wait(&bar[s], (unsigned)((it / kTcRaw) & 1));  // raw stage arrived
+        if (ok) pend[s] = -1;
+        if (it >= 1) ok = ok && mbar_wait(mbar, (unsigned)((it - 1) & 1));  // the operands are free
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            s_bad = 1;
+            break;
+        }
+        tc_fence_after();
+        if (undrained) drain(prevN);  // the previous chunk's MMAs are complete
+        tc_convert((const float2*)raw(s), ld, ro, NR, ncol, Kpad, xs, nrhs_pad, nrhs, A, A2, B, tid);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();  // operands written; the raw stage is free again
+        if (c + kTcRaw < ce) {
+            batch_issue<float>(g, recs, c + kTcRaw, raw(s), &bar[s], nrhs, nrhs_pad, bulk_x, tid, kTcThreads);
+            pend[s] = ((it + kTcRaw) / kTcRaw) & 1;
+        }
+        if (tid == 0) {
+            tc_fence_after();
+            const int N = 2 * NR;
+            const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+            const unsigned sbo = (unsigned)(Kpad >> 2) << 7;
+            const unsigned a0 = smem_u32(A), a20 = smem_u32(A2), b0 = smem_u32(B);
+            for (int st = 0; st < Kpad / 8; st++) {
+                const unsigned long long ad = tc_desc(a0 + 256 * st, 128, sbo);
+                const unsigned long long bh = tc_desc(b0 + 256 * st, 128, sbo);
+                tc_mma(tmem, ad, bh, idesc, st == 0 ? 0u : 1u);
+                tc_mma(tmem, ad, tc_desc(b0 + kTcBPart + 256 * st, 128, sbo), idesc, 1u);
+                tc_mma(tmem, ad, tc_desc(b0 + 2 * kTcBPart + 256 * st, 128, sbo), idesc, 1u);
+                tc_mma(tmem, tc_desc(a20 + 256 * st, 128, sbo), bh, idesc, 1u);
+            }
+            tc_commit(mbar);
+        }
+        issued = it + 1;
+        undrained = true;
+        prevN = 2 * NR;
+        const bool row_ends = (c + 1 == ce) || recs[2 * (c + 1)].x != ra.x || recs[2 * (c + 1)].y != ra.y;
+        if (!row_ends) continue;
+        // the row's accumulator: wait for its last MMAs, drain, columns to E[n][lane]
+        ok = mbar_wait(mbar, (unsigned)(it & 1));
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            s_bad = 1;
+            break;
+        }
+        tc_fence_after();
+        drain(prevN);
+        undrained = false;
+        {
+            const int q = warp & 3, half = NR, col0 = (warp >> 2) * half;
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                if (j < half) {
+                    E[(col0 + j) * 128 + 32 * q + lane] = acc[j];
+                    acc[j] = 0.f;
+                }
+        }
+        tc_fence_before();
+        __syncthreads();
+        const bool direct = (ra.x & kFlagDirect) != 0;
+        const bool add = (ra.x & kFlagAdd) != 0;
+        float2* yrow = pa.y + (size_t)ra.y * pa.ldy * nrhs;
+        const int4 rbx = recs[2 * c + 1];
+        const bool whole = direct || (rbx.w >= cb && rbx.z <= ce);
+        float2* dst = whole ? yrow : P + (size_t)pslot * Pld * nrhs;
+        for (int e = tid; e < ro * nrhs; e += kTcThreads) {
+            const int i = e / nrhs, r = e - i * nrhs;
+            float re = E[i * 128 + r] + E[i * 128 + 64 + r];
+            float im = E[(NR + i) * 128 + r] + E[(NR + i) * 128 + 64 + r];
+            float2* qp = dst + (size_t)i * nrhs + r;
+            if (whole && add) {
+                const float2 o = *qp;
+                re += o.x;
+                im += o.y;
+            }
+            *qp = make_float2(re, im);
+        }
+        if (!whole) {
+            // the last CTA to write a partial of this row sums them in slot order
+            const int c0 = rbx.w, c1 = rbx.z;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(&cnt[c0], 1) + 1 == row_slots(c0, c1, 0, kpc);
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                for (int qq = tid; qq < ro * nrhs; qq += kTcThreads) {
+                    float sr = 0, si = 0;
+                    if (add) {
+                        const float2 o = yrow[qq];
+                        sr = o.x;
+                        si = o.y;
+                    }
+                    for (int cc = c0; cc < c1; cc = (cc / kpc + 1) * kpc) {
+                        const float2 p = __ldcg(&P[(size_t)cc * Pld * nrhs + qq]);
+                        sr += p.x;
+                        si += p.y;
+                    }
+                    yrow[qq] = make_float2(sr, si);
+                }
+                if (tid == 0) cnt[c0] = 0;
+            }
+        }
+        __syncthreads();  // E (the A operands) is free for the next conversion
+        pslot = c + 1;
+    }
+    if (s_bad && tid == 0) {
+        // let this CTA's copies and MMAs in flight land (bounded) before the TMEM goes
+        for (int k = 0; k < kTcRaw; k++)
+            if (pend[k] >= 0) mbar_wait(&bar[k], (unsigned)pend[k]);
+        if (issued > 0) mbar_wait(mbar, (unsigned)((issued - 1) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
 // Batched leaf kernel: one CTA per leaf, threads over (node i, rhs r), rhs fastest.
 template <typename T>
 __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__ nbr, const typename V2<T>::t* __restrict__ near,
@@ -2250,6 +2594,40 @@ void launch_batched_mr(const OpsDev& d, const Group& g, const GroupArgs<T>& ga, 
     }
 }
 
+// Several right-hand sides, complex64, on the tensor cores (one CTA per SM:
+// its operand buffers take most of the shared memory).
+void launch_batched_tc(const OpsDev& d, const Group& g, const GroupArgs<float>& ga, float2* part, int nrhs, cudaStream_t s)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int nrhs_pad = (nrhs + kRhsPerWarp - 1) / kRhsPerWarp * kRhsPerWarp;
+    const int smem = tc_smem_bytes(nrhs_pad);
+    CK(cudaFuncSetAttribute(stream_batched_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_batched_tc_kernel, kTcThreads, smem));
+    per_sm = std::max(per_sm, 1);
+    const int ctas = std::max(1, std::min(g.nch, sms * per_sm));
+    const int kpc = (g.nch + ctas - 1) / ctas;
+    const int grid = (g.nch + kpc - 1) / kpc;
+    int bulk_x = (nrhs * (int)sizeof(float2)) % 16 == 0;
+    for (size_t p = 0; p < g.passes.size(); p++) bulk_x &= ((uintptr_t)ga.p[p].x % 16) == 0;
+    stream_batched_tc_kernel<<<(unsigned)grid, kTcThreads, smem, s>>>(g.nch, kpc, nrhs, nrhs_pad, bulk_x, g.chunks, ga, part, g.Pld, g.cnt,
+                                                                      d.err);
+}
+
+// Tensor cores for the complex64 several-right-hand-side passes (see
+// dafmm_set_batched_kernel).  Automatic mode keeps the CUDA-core kernel: at
+// these chunk shapes (M = 128 stacked rows, N = 2 NR <= 128, K <= 64 per
+// chunk) the operand conversion and the serial per-chunk steps cost more than
+// the FMAs they replace (64 right-hand sides at N = 16384: 1.59 ms on the
+// tensor cores, 0.74 ms on the CUDA cores).
+constexpr int kTcMinRhs = 8;
+constexpr bool kTcAuto = false;
+
 template <typename T>
 void launch_group_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, const typename V2<T>::t* vin, const Group& g, int nrhs,
                           cudaStream_t s)
@@ -2258,6 +2636,13 @@ void launch_group_batched(const Tree& t, const OpsDev& d, const Bufs<T>& b, cons
     GroupArgs<T> ga;
     std::memset(&ga, 0, sizeof(ga));
     for (size_t p = 0; p < g.passes.size(); p++) ga.p[p] = pass_args<T>(t, d, b, vin, g, (int)p);
+    if constexpr (sizeof(T) == 4) {
+        const bool tc = d.batched_kernel == 2 || (d.batched_kernel == 0 && kTcAuto && nrhs >= kTcMinRhs);
+        if (tc && g.Pld <= 64) {
+            launch_batched_tc(d, g, ga, b.part, nrhs, s);
+            return;
+        }
+    }
     const int h = ((g.Pld + 3) >> 2) << 1;  // rows per lane of the widest row
     if (h <= 8)
         launch_batched_mr<T, 8>(d, g, ga, b.part, nrhs, s);
@@ -2453,6 +2838,20 @@ void ensure_scratch(const Tree& t, OpsDev& d, int nrhs)
     d.part = nullptr;
     dev_alloc((double2**)&d.part, sizeof(double2) * std::max<size_t>(d.part_elems, 1) * nrhs);
     d.nrhs_cap = nrhs;
+    for (auto& row : d.gc)
+        for (auto& G : row) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.graph) cudaGraphDestroy(G.graph);
+            G = GraphCache();
+        }
+}
+
+void set_batched_kernel(OpsDev& d, int mode)
+{
+    if (mode < 0 || mode > 2) fail(DAFMM_EBADARG, "batched kernel: 0 automatic, 1 CUDA cores, 2 tensor cores");
+    if (mode == d.batched_kernel) return;
+    d.batched_kernel = mode;
+    // captured applications hold the previous kernels
     for (auto& row : d.gc)
         for (auto& G : row) {
             if (G.exec) cudaGraphExecDestroy(G.exec);

@@ -419,6 +419,14 @@ int dafmm_sync(dafmm_ops* ops, void* stream)
     return r;
 }
 
+int dafmm_set_batched_kernel(dafmm_ops* ops, int mode)
+{
+    return guarded([&] {
+        if (!ops) fail(DAFMM_EBADARG, "NULL argument");
+        set_batched_kernel(ops->dev, mode);
+    });
+}
+
 int dafmm_set_contrast(dafmm_ops* ops, const double* q_dev, void* stream)
 {
     return guarded([&] {

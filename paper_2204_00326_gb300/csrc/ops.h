@@ -134,12 +134,14 @@ struct OpsDev {
     unsigned long long gc_clock = 0;
     GmresWork* gw = nullptr;
     GmresMany* gm = nullptr;
+    int batched_kernel = 0;     // several right-hand sides, complex64: 0 automatic, 1 CUDA cores, 2 tensor cores
 };
 
 // Allocate and upload; frees host block storage as it goes.
 void upload_ops(const Tree& t, OpsHost& h, OpsDev& d);
 void free_ops(OpsDev& d);
 void profile_enable(OpsDev& d, bool on);
+void set_batched_kernel(OpsDev& d, int mode);
 void profile_read(OpsDev& d, dafmm_profile_t& p);
 // Make sure scratch holds nrhs right-hand sides.
 void ensure_scratch(const Tree& t, OpsDev& d, int nrhs);

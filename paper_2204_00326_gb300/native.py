@@ -158,6 +158,7 @@ _sig = {
     "build_nca_operators": ([_P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "dafmm_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "dafmm_set_batched_kernel": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_potential": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -293,6 +294,15 @@ def dafmm_matvec_noalloc(ops: int, v, out, precision: int = DAFMM_FP64, stream=N
     if v.dim() != 1 or out.shape != v.shape:
         raise ValueError("one right-hand side: v and out are (N,) vectors")
     _check(lib.dafmm_matvec_noalloc(ops, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
+
+
+BATCHED_AUTO, BATCHED_CUDA_CORES, BATCHED_TENSOR_CORES = 0, 1, 2
+
+
+def dafmm_set_batched_kernel(ops: int, mode: int) -> None:
+    """Kernel of the complex64 tree passes with several right-hand sides:
+    0 automatic, 1 CUDA cores, 2 tensor cores (tcgen05, split tf32)."""
+    _check(lib.dafmm_set_batched_kernel(ops, int(mode)))
 
 
 def dafmm_sync(ops: int, stream=None) -> None:

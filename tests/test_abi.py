@@ -98,6 +98,7 @@ def test_null_and_device_errors_are_status_codes():
     assert lib.hodlr_debug_stall(None) == N.DAFMM_EBADARG
     assert lib.hodlr_solve(None, 1, None, None, 0, None) == N.DAFMM_EBADARG
     assert lib.gmres_solve(None, None, 1, None, None, None, None, None) == N.DAFMM_EBADARG
+    assert lib.dafmm_set_batched_kernel(None, 0) == N.DAFMM_EBADARG
     buf = ctypes.create_string_buffer(256)
     assert lib.dafmm_last_error(buf, 256) == N.DAFMM_EBADARG
     assert b"NULL" in buf.value

@@ -68,8 +68,21 @@ typedef struct dafmm_params {
     double eps_nca;   /* tolerance of the partially pivoted ACA that picks the
                          NCA pivots (Section 4.2.2, Rjasanow's stopping rule) */
     int max_rank;     /* cap on every NCA rank; 0 = no cap */
-    int reserved[7];  /* must be zero */
+    int kernel;       /* the matrix K the DAFMM compresses: DAFMM_KERNEL_LS (0) or
+                         DAFMM_KERNEL_POINTS (1), see below */
+    int reserved[6];  /* must be zero */
 } dafmm_params;
+
+/*
+ * Kernels.  DAFMM_KERNEL_LS: K_ij = int_{B(j)} G(x_i, y) L_{j'}(y) dy, the
+ * discretised volume integral of Eq. 13 (the Lippmann-Schwinger operator).
+ * DAFMM_KERNEL_POINTS: K_ij = G(x_i, x_j) for j != i and K_ii = 0, the point
+ * N-body operator of Experiment 1 (Section 6.2) with charges at the same
+ * Chebyshev nodes; dafmm_potential then returns u = K v, and
+ * dafmm_nbody_direct gives the same sum by direct summation.
+ */
+#define DAFMM_KERNEL_LS 0
+#define DAFMM_KERNEL_POINTS 1
 
 /* Shape of a built tree (filled by tree_info). */
 typedef struct dafmm_tree_info {
@@ -185,6 +198,11 @@ int build_tree(const dafmm_params* params, int n_side, double x0, double x1, daf
 
 /* Coordinates of the N unknowns (xy_host: N x 2 doubles, caller-owned). */
 int tree_nodes(const dafmm_tree* tree, double* xy_host);
+
+/* The same coordinates into device memory (xy_dev: N x 2 doubles,
+ * caller-owned), copied on stream; synchronises the stream.  Errors:
+ * DAFMM_EBADARG for NULL arguments, DAFMM_ECUDA. */
+int tree_nodes_dev(const dafmm_tree* tree, double* xy_dev, void* stream);
 
 /* Shape of the tree (see dafmm_tree_info). */
 int tree_info(const dafmm_tree* tree, dafmm_tree_info* info);
@@ -428,6 +446,19 @@ int dafmm_debug_stall(dafmm_ops* ops, int pass);
  * changes.  Errors: DAFMM_EBADARG for a NULL handle or a mode outside 0..2.
  */
 int dafmm_set_batched_kernel(dafmm_ops* ops, int mode);
+
+/*
+ * dafmm_nbody_direct -- u_i = sum_{j != i} G(x_i, x_j) v_j over the tree's N
+ * nodes by direct summation, O(N^2) (the reference of Experiment 1, Section
+ * 6.2): one warp per target, the Hankel function H0^(1) = J0 + i Y0
+ * evaluated in registers for every source (FP64), the partial sums of the
+ * lanes combined by warp shuffles.  Uses the tree's kappa whatever its
+ * kernel.  v_dev, out_dev: N complex128 on the device (must not overlap).
+ * Allocates N x 2 doubles of node coordinates for the call (stream-ordered)
+ * and synchronises the stream once, after copying them; the sum itself is
+ * asynchronous on stream.  Errors: DAFMM_EBADARG, DAFMM_ENOMEM, DAFMM_ECUDA.
+ */
+int dafmm_nbody_direct(const dafmm_tree* tree, const double* v_dev, double* out_dev, void* stream);
 
 /* Realised ranks, operator bytes and work of one application. */
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats);

@@ -65,6 +65,7 @@ def _load():
         lib.or_grid_nodes.argtypes = [i, d, d, i, P]
         lib.or_K_rows.argtypes = [i, d, d, i, d, l, P, P]
         lib.or_matvec_rows.argtypes = [i, d, d, i, d, P, i, P, l, P, P]
+        lib.or_nbody_rows.argtypes = [i, d, d, i, d, i, P, l, P, P]
         lib.or_lu_solve.argtypes = [l, P, i, P]
         lib.or_num_threads.argtypes = []
         _lib = lib
@@ -192,6 +193,26 @@ def matvec_rows(n_side: int, kappa: float, q, v, rows, x0: float = -1.0, x1: flo
     out = np.zeros((len(rows), nrhs, 2))
     st = _load().or_matvec_rows(n_side, x0, x1, p, float(kappa), _ptr(qq), nrhs, _ptr(vv), len(rows), _ptr(rows), _ptr(out))
     _check(st, "matvec_rows")
+    res = out[..., 0] + 1j * out[..., 1]
+    return res[:, 0] if squeeze else res
+
+
+def nbody_rows(n_side: int, kappa: float, v, rows, x0: float = -1.0, x1: float = 1.0, p: int = 4) -> np.ndarray:
+    """u_i = sum_{j != i} G(p_i, p_j) v_j at the grid nodes for the listed rows
+    (Experiment 1's N-body potential, Section 6.2), by direct summation.
+
+    ``v`` is (N,) or (N, nrhs) complex; returns (len(rows),) or (len(rows), nrhs).
+    """
+    v = np.asarray(v, dtype=np.complex128)
+    squeeze = v.ndim == 1
+    v2 = v.reshape(v.shape[0], -1)
+    nrhs = v2.shape[1]
+    if nrhs > 64:
+        raise ValueError("oracle nbody_rows handles at most 64 right-hand sides")
+    vv = np.ascontiguousarray(np.stack([v2.real, v2.imag], axis=-1))
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    out = np.zeros((len(rows), nrhs, 2))
+    _check(_load().or_nbody_rows(n_side, x0, x1, p, float(kappa), nrhs, _ptr(vv), len(rows), _ptr(rows), _ptr(out)), "nbody_rows")
     res = out[..., 0] + 1j * out[..., 1]
     return res[:, 0] if squeeze else res
 

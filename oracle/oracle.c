@@ -19,7 +19,9 @@
  *     L_{j'} = sum_l Q^+_{l,j'} b_l is the least-squares cardinal function
  *     of Eq. 11, so that A = I + kappa^2 diag(q) K (Eq. 13);
  *   - rows of K, the matrix-vector product A v row by row, and a plain
- *     Gaussian-elimination LU solve of A psi = f (Eq. 12a).
+ *     Gaussian-elimination LU solve of A psi = f (Eq. 12a);
+ *   - the point N-body potential of Experiment 1 (Section 6.2) by direct
+ *     summation over the same nodes.
  *
  * Quadrature (a reading: the paper names "adaptive Gauss quadrature" and
  * Boost's Hankel function, Section 2.3, but gives no rule): the reference
@@ -506,6 +508,45 @@ int or_matvec_rows(int n_side, double x0, double x1, int p, double kappa, const 
     }
     free(g.Qp);
     return err;
+}
+
+/*
+ * Experiment 1's N-body potential (Section 6.2): charges v_j at the grid
+ * nodes p_j, u_i = sum_{j != i} G(p_i, p_j) v_j with G = (i/4) H0^(1)(kappa
+ * |p_i - p_j|), by direct summation for the listed rows (the paper's sum
+ * runs over every j; the j = i term is singular and left out, a reading).
+ * v, out complex interleaved, [N][nrhs].
+ */
+int or_nbody_rows(int n_side, double x0, double x1, int p, double kappa, int nrhs, const double* v, long nrows, const long* rows,
+                  double* out)
+{
+    grid_ctx g;
+    int st = grid_init(&g, n_side, x0, x1, p, kappa);
+    if (st) { free(g.Qp); return st; }
+    const long N = (long)n_side * n_side;
+    double* xy = (double*)malloc(sizeof(double) * 2 * N);
+    if (!xy) { free(g.Qp); return 2; }
+    for (long j = 0; j < N; j++) point_xy(&g, j, &xy[2 * j], &xy[2 * j + 1]);
+    int nr = nrhs > 64 ? 64 : nrhs;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long r = 0; r < nrows; r++) {
+        long i = rows[r];
+        cplx acc[64];
+        for (int k = 0; k < nr; k++) acc[k] = 0.0;
+        for (long j = 0; j < N; j++) {
+            if (j == i) continue;
+            double dx = xy[2 * i] - xy[2 * j], dy = xy[2 * i + 1] - xy[2 * j + 1];
+            cplx gij = green(kappa, sqrt(dx * dx + dy * dy));
+            for (int k = 0; k < nr; k++) acc[k] += gij * (v[2 * (j * nrhs + k)] + I * v[2 * (j * nrhs + k) + 1]);
+        }
+        for (int k = 0; k < nr; k++) {
+            out[2 * (r * nrhs + k)] = creal(acc[k]);
+            out[2 * (r * nrhs + k) + 1] = cimag(acc[k]);
+        }
+    }
+    free(xy);
+    free(g.Qp);
+    return 0;
 }
 
 /*

@@ -151,18 +151,26 @@ int tree_nodes(const dafmm_tree* tree, double* xy)
 {
     return guarded([&] {
         if (!tree || !xy) fail(DAFMM_EBADARG, "NULL argument");
-        const Tree& t = tree->t;
-        double z[16];
-        cheb_nodes(t.p, z);
-        const int n2 = t.p * t.p;
-        for (long i = 0; i < t.N; i++) {
-            long leaf = i / n2;
-            int ip = (int)(i % n2);
-            double ax = t.x0 + (2.0 * t.leaf_x[leaf] + 1.0) * t.beta;
-            double ay = t.x0 + (2.0 * t.leaf_y[leaf] + 1.0) * t.beta;
-            xy[2 * i] = ax + t.beta * z[ip % t.p];
-            xy[2 * i + 1] = ay + t.beta * z[ip / t.p];
-        }
+        node_coords(tree->t, xy);
+    });
+}
+
+int tree_nodes_dev(const dafmm_tree* tree, double* xy_dev, void* stream)
+{
+    return guarded([&] {
+        if (!tree || !xy_dev) fail(DAFMM_EBADARG, "NULL argument");
+        require_device();
+        node_coords_dev(tree->t, xy_dev, (cudaStream_t)stream);
+    });
+}
+
+int dafmm_nbody_direct(const dafmm_tree* tree, const double* v, double* out, void* stream)
+{
+    return guarded([&] {
+        if (!tree || !v || !out) fail(DAFMM_EBADARG, "NULL argument");
+        if (v == out) fail(DAFMM_EBADARG, "v and out must not overlap");
+        require_device();
+        nbody_direct(tree->t, v, out, (cudaStream_t)stream);
     });
 }
 

@@ -1,5 +1,5 @@
-// Device-built table of the matrix entries of Eq. 13 for every leaf offset of
-// the uniform grid.  On a uniform tree K_ij depends only on the offset between
+// Device-built table of the matrix entries of Eq. 13 (or of the point
+// kernel of Experiment 1) for every leaf offset of the uniform grid.  On a uniform tree K_ij depends only on the offset between
 // the target's and the source's leaves and on (i', j'), so one table per leaf
 // level holds every entry (the paper tabulates its near- and far-field
 // integrals once per level for the same reason, Section 2.3).
@@ -214,6 +214,27 @@ __global__ void near_table_kernel(int nb, double kb, double beta2, double2* tab)
     write_row(sh + 32 * 2 * kNp, beta2, tab + (off * 16 + ip) * 16);
 }
 
+// Point kernel (Experiment 1's N-body operator): K(offset, i', j') =
+// G(x_i', x_j') = (i/4) H0^(1)(kappa beta |t - zeta_j'|), t = 2 offset +
+// zeta_i' in the source box's reference frame; zero for i = j.  One thread
+// per table entry.
+__global__ void point_table_kernel(int nb, double kb, double2* tab)
+{
+    const long noff = (long)(2 * nb - 1) * (2 * nb - 1);
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= noff * 256) return;
+    const int jp = (int)(e & 15), ip = (int)((e >> 4) & 15);
+    const long off = e >> 8;
+    const int dx = (int)(off % (2 * nb - 1)) - (nb - 1), dy = (int)(off / (2 * nb - 1)) - (nb - 1);
+    if (dx == 0 && dy == 0 && ip == jp) {
+        tab[e] = make_double2(0.0, 0.0);
+        return;
+    }
+    const double tx = 2.0 * dx + c_z[ip & 3] - c_z[jp & 3], ty = 2.0 * dy + c_z[ip >> 2] - c_z[jp >> 2];
+    const double z = kb * hypot(tx, ty);
+    tab[e] = make_double2(-0.25 * y0(z), 0.25 * j0(z));
+}
+
 #define CK(x)                                                                                     \
     do {                                                                                          \
         cudaError_t e_ = (x);                                                                     \
@@ -267,11 +288,17 @@ double build_entry_table(const Tree& t, EntryTable& out, void* stream_)
         fail(DAFMM_ENOMEM, "device allocation of the entry table failed");
     }
     const double kb = t.prm.kappa * t.beta, beta2 = t.beta * t.beta;
-    near_table_kernel<<<9 * 16, 256, 0, stream>>>(nb, kb, beta2, d_tab);
-    cudaError_t e1 = cudaGetLastError();
-    if (nb >= 3 && e1 == cudaSuccess) {
-        far_table_kernel<<<(unsigned)(noff * 16), 256, 0, stream>>>(nb, kb, beta2, d_tab);
+    cudaError_t e1 = cudaSuccess;
+    if (t.prm.kernel == DAFMM_KERNEL_POINTS) {
+        point_table_kernel<<<(unsigned)((noff * 256 + 255) / 256), 256, 0, stream>>>(nb, kb, d_tab);
         e1 = cudaGetLastError();
+    } else {
+        near_table_kernel<<<9 * 16, 256, 0, stream>>>(nb, kb, beta2, d_tab);
+        e1 = cudaGetLastError();
+        if (nb >= 3 && e1 == cudaSuccess) {
+            far_table_kernel<<<(unsigned)(noff * 16), 256, 0, stream>>>(nb, kb, beta2, d_tab);
+            e1 = cudaGetLastError();
+        }
     }
     out.nb = nb;
     out.tab.resize((size_t)noff * 256);

@@ -193,6 +193,12 @@ void unet_apply_nodes(dafmm_unet* u, const Tree& t, const OpsDev& d, const doubl
 double relative_residual(const Tree& t, OpsDev& d, const double* f, const double* x, double* tmp, double* scal, cudaStream_t s);
 double* unet_scalars(dafmm_unet* u);  // 2 device doubles owned by the network
 
+// Node coordinates (N x 2, the documented order) on the host or, synchronising
+// s, copied to the device; the direct N-body sum of Experiment 1 (nbody.cu).
+void node_coords(const Tree& t, double* xy);
+void node_coords_dev(const Tree& t, double* xy_dev, cudaStream_t s);
+void nbody_direct(const Tree& t, const double* v, double* out, cudaStream_t s);
+
 // Kernels one application launches.
 int launches_per_call(const Tree& t, const OpsDev& d, int precision);
 // Synchronise the stream and report (and clear) a device-side wait timeout.

@@ -103,6 +103,8 @@ Tree* make_tree(const dafmm_params& prm, int n_side, double x0, double x1)
     if (!(prm.eps_nca > 0 && prm.eps_nca < 1)) fail(DAFMM_EBADARG, "eps_nca must lie in (0, 1)");
     if (!(prm.T > 0)) fail(DAFMM_EBADARG, "T must be positive");
     if (prm.max_rank < 0) fail(DAFMM_EBADARG, "max_rank must be >= 0");
+    if (prm.kernel != DAFMM_KERNEL_LS && prm.kernel != DAFMM_KERNEL_POINTS)
+        fail(DAFMM_EBADARG, "kernel must be DAFMM_KERNEL_LS or DAFMM_KERNEL_POINTS");
     for (int r : prm.reserved)
         if (r) fail(DAFMM_EBADARG, "reserved parameters must be zero");
     if (!(x1 > x0)) fail(DAFMM_EBADARG, "x1 must exceed x0");

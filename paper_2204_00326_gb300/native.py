@@ -44,7 +44,8 @@ class dafmm_params(ctypes.Structure):
         ("T", ctypes.c_double),
         ("eps_nca", ctypes.c_double),
         ("max_rank", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("kernel", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 
@@ -159,6 +160,8 @@ _sig = {
     "dafmm_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_matvec_noalloc": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_set_batched_kernel": ([_P, ctypes.c_int], ctypes.c_int),
+    "dafmm_nbody_direct": ([_P, _P, _P, _P], ctypes.c_int),
+    "tree_nodes_dev": ([_P, _P, _P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_potential": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -226,13 +229,18 @@ def _dptr(t, dtype_name: str) -> int:
     return int(t.data_ptr())
 
 
-def make_params(kappa: float, eps_nca: float = 1e-12, T: float = 16.0, p: int = 4, max_rank: int = 0) -> dafmm_params:
+DAFMM_KERNEL_LS, DAFMM_KERNEL_POINTS = 0, 1
+
+
+def make_params(kappa: float, eps_nca: float = 1e-12, T: float = 16.0, p: int = 4, max_rank: int = 0,
+                kernel: int = DAFMM_KERNEL_LS) -> dafmm_params:
     prm = dafmm_params()
     prm.p = p
     prm.kappa = kappa
     prm.T = T
     prm.eps_nca = eps_nca
     prm.max_rank = max_rank
+    prm.kernel = kernel
     return prm
 
 
@@ -240,6 +248,11 @@ def build_tree(params: dafmm_params, n_side: int, x0: float = -1.0, x1: float = 
     h = _P()
     _check(lib.build_tree(ctypes.byref(params), n_side, x0, x1, ctypes.byref(h)))
     return h.value
+
+
+def tree_nodes_dev(tree: int, xy, stream=None) -> None:
+    """Node coordinates into a (N, 2) float64 CUDA tensor."""
+    _check(lib.tree_nodes_dev(tree, _dptr(xy, "float64"), _stream_ptr(stream)))
 
 
 def tree_nodes(tree: int, N: int) -> np.ndarray:
@@ -294,6 +307,13 @@ def dafmm_matvec_noalloc(ops: int, v, out, precision: int = DAFMM_FP64, stream=N
     if v.dim() != 1 or out.shape != v.shape:
         raise ValueError("one right-hand side: v and out are (N,) vectors")
     _check(lib.dafmm_matvec_noalloc(ops, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
+
+
+def dafmm_nbody_direct(tree: int, v, out, stream=None) -> None:
+    """u_i = sum_{j != i} G(x_i, x_j) v_j by direct summation on the device."""
+    if v.dim() != 1 or out.shape != v.shape:
+        raise ValueError("v and out are (N,) vectors")
+    _check(lib.dafmm_nbody_direct(tree, _dptr(v, "complex128"), _dptr(out, "complex128"), _stream_ptr(stream)))
 
 
 BATCHED_AUTO, BATCHED_CUDA_CORES, BATCHED_TENSOR_CORES = 0, 1, 2

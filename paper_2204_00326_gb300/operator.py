@@ -16,11 +16,11 @@ class DafmmOperator:
     """
 
     def __init__(self, n_side: int, kappa: float, contrast, eps_nca: float = 1e-12, T: float = 16.0,
-                 x0: float = -1.0, x1: float = 1.0, stream=None):
+                 x0: float = -1.0, x1: float = 1.0, stream=None, kernel: int = N.DAFMM_KERNEL_LS):
         self.n_side = n_side
         self.kappa = kappa
         self.N = n_side * n_side
-        self.params = N.make_params(kappa, eps_nca=eps_nca, T=T)
+        self.params = N.make_params(kappa, eps_nca=eps_nca, T=T, kernel=kernel)
         self.tree = N.build_tree(self.params, n_side, x0, x1)
         self.ops = None
         self.xy = N.tree_nodes(self.tree, self.N)
@@ -28,6 +28,13 @@ class DafmmOperator:
         self.q = np.ascontiguousarray(q, dtype=np.float64)
         q_dev = torch.as_tensor(self.q, device="cuda")
         self.ops = N.build_nca_operators(self.tree, q_dev, stream)
+
+    def potential(self, v: torch.Tensor, out: torch.Tensor | None = None, precision: int = N.DAFMM_FP64, stream=None):
+        """K v: the volume potential (or, with the point kernel, the N-body potential)."""
+        if out is None:
+            out = torch.empty_like(v)
+        N.dafmm_potential(self.ops, v, out, precision, stream)
+        return out
 
     def matvec(self, v: torch.Tensor, out: torch.Tensor | None = None, precision: int = N.DAFMM_FP64, stream=None):
         if out is None:

@@ -43,6 +43,11 @@ GRID32_K8 = Workload("grid32_k8_gauss", 32, 8.0, "gauss_trunc", tol=1e-10)
 GRID128_K40 = Workload("grid128_k40_bumps4", 128, 40.0, "bumps", nbumps=4, seed=0)
 GRID256_K80 = Workload("grid256_k80_disc", 256, 80.0, "disc", nrhs=64)
 GRID512_K160 = Workload("grid512_k160_bumps8", 512, 160.0, "bumps", nbumps=8, seed=1)
+# Experiment 1 (Section 6.2): point charges at the Chebyshev nodes of a uniform
+# grid on [-1,1]^2, kappa = 50, random charges; the paper uses p = 10 nodes per
+# leaf side on 32 x 32 leaves (N = 102400), the library p = 4 on 64 x 64
+# leaves (N = 65536, leaf kappa w = 0.78, low frequency as in the paper).
+NBODY256_K50 = Workload("nbody256_k50", 256, 50.0, "zero")
 WORKLOADS = {w.name: w for w in (GRID32_K8, GRID128_K40, GRID256_K80, GRID512_K160)}
 
 
@@ -52,6 +57,8 @@ def contrast(w: Workload, xy: np.ndarray) -> np.ndarray:
     r2 = x * x + y * y
     if w.contrast == "gauss_trunc":
         return np.where(r2 <= 0.81, 1.5 * np.exp(-16.0 * r2), 0.0)
+    if w.contrast == "zero":
+        return np.zeros(len(x))
     if w.contrast == "disc":
         return np.where(r2 < 0.25, 2.0, 0.0)
     if w.contrast == "bumps":

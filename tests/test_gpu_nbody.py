@@ -1,0 +1,141 @@
+"""Experiment 1 (Section 6.2): the point N-body potential
+u_i = sum_{j != i} G(p_i, p_j) f_j at the Chebyshev nodes of a uniform grid,
+kappa = 50, by the DAFMM (kernel DAFMM_KERNEL_POINTS, dafmm_potential) and by
+direct summation on the GPU (dafmm_nbody_direct), against the oracle's
+direct sum.
+
+Tolerances: the direct GPU sum is FP64 over the same nodes, checked at 1e-11
+relative 2-norm (the device's and the C library's FP64 Bessel functions
+differ by ~1e-12 at the large arguments kappa |p_i - p_j| reaches; measured
+3.5e-12 on sums of 65536 terms); the DAFMM's error tracks
+eps_nca (the paper's Figure on error against eps_nca): 1e-10 at eps_nca =
+1e-12 in FP64, 2e-5 in mixed precision (complex64 operators).  The point
+kernel carries no kappa^2 factor, unlike Eq. 13's A.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2204_00326_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    import paper_2204_00326_gb300 as pkg
+
+    pkg.build()
+    from paper_2204_00326_gb300 import native
+
+    return native
+
+
+def _op(N, n_side, kappa, eps=1e-12):
+    from paper_2204_00326_gb300.operator import DafmmOperator
+
+    return DafmmOperator(n_side, kappa, np.zeros(n_side * n_side), eps_nca=eps, kernel=N.DAFMM_KERNEL_POINTS)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_small_grid_against_the_oracle_everywhere(N):
+    """64 x 64 nodes (16 x 16 leaves, leaf kappa w = 3.1): every row."""
+    n, kappa = 64, 50.0
+    op = _op(N, n, kappa)
+    try:
+        f = W.random_vector(op.N, 1, seed=60)[:, 0]
+        ref = O.nbody_rows(n, kappa, f, np.arange(op.N))
+        fd = torch.as_tensor(f, device="cuda")
+        direct = torch.empty_like(fd)
+        N.dafmm_nbody_direct(op.tree, fd, direct)
+        assert _rel(direct.cpu().numpy(), ref) < 1e-11
+        assert _rel(op.potential(fd, precision=N.DAFMM_FP64).cpu().numpy(), ref) < 1e-10
+        assert _rel(op.potential(fd, precision=N.DAFMM_MIXED).cpu().numpy(), ref) < 2e-5
+        # several charge vectors at once (the batched passes)
+        F = W.random_vector(op.N, 8, seed=61)
+        U = op.potential(torch.as_tensor(F, device="cuda").contiguous(), precision=N.DAFMM_FP64).cpu().numpy()
+        rows = np.arange(0, op.N, 97)
+        R = O.nbody_rows(n, kappa, F, rows)
+        assert (np.linalg.norm(U[rows] - R, axis=0) / np.linalg.norm(R, axis=0)).max() < 1e-10
+        op.sync()
+    finally:
+        op.close()
+
+
+def test_error_tracks_eps_nca(N):
+    """The DAFMM error falls with eps_nca (Experiment 1's error plot)."""
+    n, kappa = 64, 50.0
+    f = W.random_vector(n * n, 1, seed=62)[:, 0]
+    ref = O.nbody_rows(n, kappa, f, np.arange(n * n))
+    errs = []
+    for eps in (1e-4, 1e-7, 1e-10):
+        op = _op(N, n, kappa, eps)
+        try:
+            errs.append(_rel(op.potential(torch.as_tensor(f, device="cuda"), precision=N.DAFMM_FP64).cpu().numpy(), ref))
+        finally:
+            op.close()
+    assert errs[0] > 30 * errs[1] > 900 * errs[2], errs
+    assert errs[0] < 1e-2 and errs[2] < 1e-8
+
+
+def test_point_kernel_table_is_the_green_function(N):
+    """The library's entries are G(p_i, p_j) with a zero diagonal."""
+    from scipy.special import hankel1
+
+    n, kappa = 64, 50.0
+    op = _op(N, n, kappa)
+    try:
+        rows = np.array([0, 17, 300, 1023, 4095])
+        got = op.entries(rows, np.arange(op.N))
+        d = np.hypot(op.xy[rows, None, 0] - op.xy[None, :, 0], op.xy[rows, None, 1] - op.xy[None, :, 1])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ref = np.where(d > 0, 0.25j * hankel1(0, kappa * np.where(d > 0, d, 1.0)), 0.0)
+        # the device's and scipy's Bessel functions differ by ~1e-13 absolute
+        assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+    finally:
+        op.close()
+
+
+def test_experiment1_size_against_direct_sum(N):
+    """N = 65536 (256 x 256 nodes, 64 x 64 leaves), kappa = 50: the whole
+    DAFMM potential against the GPU's direct sum, and sampled rows of both
+    against the oracle.  At this size eps_nca = 1e-13 keeps the DAFMM within
+    1e-10 (3.3e-10 at 1e-12; the error follows eps_nca)."""
+    w = W.NBODY256_K50
+    op = _op(N, w.n_side, w.kappa, eps=1e-13)
+    try:
+        f = W.random_vector(w.N, 1, seed=63)[:, 0]
+        fd = torch.as_tensor(f, device="cuda")
+        direct = torch.empty_like(fd)
+        N.dafmm_nbody_direct(op.tree, fd, direct)
+        d = direct.cpu().numpy()
+        rows = np.sort(np.random.default_rng(64).choice(w.N, 24, replace=False))
+        ref = O.nbody_rows(w.n_side, w.kappa, f, rows)
+        assert _rel(d[rows], ref) < 1e-11
+        u = op.potential(fd, precision=N.DAFMM_FP64).cpu().numpy()
+        assert _rel(u, d) < 1e-10
+        um = op.potential(fd, precision=N.DAFMM_MIXED).cpu().numpy()
+        assert _rel(um, d) < 2e-5
+        op.sync()
+    finally:
+        op.close()
+
+
+def test_nbody_argument_errors(N):
+    op = _op(N, 64, 50.0)
+    try:
+        v = torch.zeros(op.N, dtype=torch.complex128, device="cuda")
+        with pytest.raises(N.DafmmError):
+            N.dafmm_nbody_direct(op.tree, v, v)
+        xy = torch.empty(op.N, 2, dtype=torch.float64, device="cuda")
+        N.tree_nodes_dev(op.tree, xy)
+        assert np.array_equal(xy.cpu().numpy(), op.xy)
+    finally:
+        op.close()
+    with pytest.raises(N.DafmmError):
+        N.build_tree(N.make_params(50.0, kernel=2), 64)

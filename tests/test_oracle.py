@@ -238,3 +238,36 @@ def test_solution_satisfies_lippmann_schwinger_identity():
     assert np.linalg.norm(A @ psi - f) / np.linalg.norm(f) < 1e-13
     rhs = -w.kappa ** 2 * q * (uinc + K @ psi)
     assert np.linalg.norm(psi - rhs) < 1e-12 * np.linalg.norm(psi)
+
+
+def test_nbody_rows_match_scipy_direct_sum():
+    """Experiment 1's potential u_i = sum_{j != i} (i/4) H0(kappa |p_i - p_j|) v_j
+    against a direct numpy sum with scipy's Hankel function, several
+    right-hand sides, on a 8 x 8 grid."""
+    from scipy.special import hankel1
+
+    n, kappa = 8, 5.0
+    xy = O.grid_nodes(n)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal((n * n, 3)) + 1j * rng.standard_normal((n * n, 3))
+    d = np.hypot(xy[:, None, 0] - xy[None, :, 0], xy[:, None, 1] - xy[None, :, 1])
+    np.fill_diagonal(d, 1.0)
+    G = 0.25j * hankel1(0, kappa * d)
+    np.fill_diagonal(G, 0.0)
+    rows = np.array([0, 5, 17, 63])
+    got = O.nbody_rows(n, kappa, v, rows)
+    ref = (G @ v)[rows]
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_nbody_matrix_is_symmetric_with_zero_diagonal():
+    """G(p_a, p_b) = G(p_b, p_a) bitwise, and the j = i term is left out."""
+    n, kappa = 8, 7.0
+    N = n * n
+    for a, b in ((3, 40), (0, 63), (12, 13)):
+        ea = np.zeros(N, complex)
+        eb = np.zeros(N, complex)
+        ea[a] = 1.0
+        eb[b] = 1.0
+        assert O.nbody_rows(n, kappa, eb, [a])[0] == O.nbody_rows(n, kappa, ea, [b])[0]
+        assert O.nbody_rows(n, kappa, ea, [a])[0] == 0.0

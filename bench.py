@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--eps-nca", type=float, default=1e-12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-residual solves")
+    ap.add_argument("--no-nbody", action="store_true", help="skip Experiment 1's N-body measurement")
     ap.add_argument("--no-batched-solve", action="store_true",
                     help="skip the 64-plane-wave solve on the 256 x 256, kappa = 80 disc workload")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides of the batched measurement (1 = skip)")
@@ -325,6 +326,51 @@ def batched_solve(N, DafmmOperator, nrhs=64, rank=15, singles=4):
     return out
 
 
+def experiment1(N, DafmmOperator, reps=10):
+    """Experiment 1 (Section 6.2): the point N-body potential of random
+    charges at the 256 x 256 Chebyshev nodes (N = 65536, kappa = 50) by the
+    DAFMM (dafmm_potential, FP64 and mixed) and by direct summation on the
+    GPU; relative errors against the direct sum for three eps_nca (the
+    paper's error against eps_nca), apply times with CUDA events."""
+    import torch
+
+    w = W.NBODY256_K50
+    f = torch.as_tensor(W.random_vector(w.N, 1, seed=65)[:, 0], device="cuda")
+    out = {"workload": w.name, "N": w.N, "kappa": w.kappa, "p": 4}
+    direct = torch.empty_like(f)
+    tree_op = None
+    rows = []
+    for eps in (1e-6, 1e-9, 1e-12):
+        t0 = time.perf_counter()
+        op = DafmmOperator(w.n_side, w.kappa, np.zeros(w.N), eps_nca=eps, kernel=N.DAFMM_KERNEL_POINTS)
+        setup = time.perf_counter() - t0
+        if tree_op is None:
+            N.dafmm_nbody_direct(op.tree, f, direct)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            N.dafmm_nbody_direct(op.tree, f, direct)
+            e1.record()
+            torch.cuda.synchronize()
+            out["direct_ms"] = e0.elapsed_time(e1)
+            tree_op = True
+        rec = {"eps_nca": eps, "setup_s": setup}
+        for name, prec in (("fp64", N.DAFMM_FP64), ("mixed", N.DAFMM_MIXED)):
+            u = op.potential(f, precision=prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                op.potential(f, u, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            rec[name] = {"ms": e0.elapsed_time(e1) / reps,
+                         "rel_error_vs_direct": (torch.linalg.norm(u - direct) / torch.linalg.norm(direct)).item()}
+        rows.append(rec)
+        op.close()
+    out["by_eps_nca"] = rows
+    return out
+
+
 def main():
     a = _args()
     w = W.WORKLOADS[a.workload]
@@ -520,6 +566,9 @@ def main():
     ttr_b = None
     if not a.no_batched_solve and world == 1:
         ttr_b = batched_solve(N, DafmmOperator)
+    exp1 = None
+    if not a.no_nbody and world == 1:
+        exp1 = experiment1(N, DafmmOperator)
 
     clk.__exit__(None, None, None)
 
@@ -545,6 +594,7 @@ def main():
         "batched": batched,
         "time_to_residual": ttr,
         "time_to_residual_batched": ttr_b,
+        "experiment1_nbody": exp1,
         "setup_s": {"total": setup_s, "entry_table": st.setup_seconds_table, "nca": st.setup_seconds_nca},
         "operator": {"bytes_fp32": st.operator_bytes_fp32, "bytes_fp64": st.operator_bytes_fp64,
                      "cmacs_per_rhs": st.cmacs_per_rhs},

@@ -448,6 +448,24 @@ int dafmm_debug_stall(dafmm_ops* ops, int pass);
 int dafmm_set_batched_kernel(dafmm_ops* ops, int mode);
 
 /*
+ * dafmm_field_eval -- the solution's fields at m arbitrary points x_k (Section
+ * 6.1, the error function E(x)): psi(x_k) = sum_l Q^+(l,:) psi_vec^B b_l((x_k
+ * - alpha^B) / beta) on the leaf B containing x_k (Eq. 7; zero outside the
+ * domain), and the volume potential u(x_k) = int_Omega G(x_k, y) psi(y) dy
+ * of that interpolant (Eq. 5), summed over every leaf with the quadrature of
+ * the entry table (the near rule within one box width of x_k, the 16 x 16
+ * rule beyond).  With them E(x) = |psi(x) + kappa^2 q(x) u(x) - f(x)| /
+ * kappa^2 for the caller's q and f.  O(m N): one CTA per point.
+ * psi_dev: N complex128 (the grid values); pts_dev: m x 2 doubles; u_dev: m
+ * complex128; psi_at_dev: m complex128 or NULL; all on the device.  The
+ * volume integral whatever the ops handle's kernel.  Allocates the N_p
+ * coefficients per leaf for the call (stream-ordered).  Asynchronous on
+ * stream.  Errors: DAFMM_EBADARG, DAFMM_ENOMEM, DAFMM_ECUDA.
+ */
+int dafmm_field_eval(const dafmm_ops* ops, const double* psi_dev, long m, const double* pts_dev, double* u_dev, double* psi_at_dev,
+                     void* stream);
+
+/*
  * dafmm_nbody_direct -- u_i = sum_{j != i} G(x_i, x_j) v_j over the tree's N
  * nodes by direct summation, O(N^2) (the reference of Experiment 1, Section
  * 6.2): one warp per target, the Hankel function H0^(1) = J0 + i Y0

@@ -66,6 +66,7 @@ def _load():
         lib.or_K_rows.argtypes = [i, d, d, i, d, l, P, P]
         lib.or_matvec_rows.argtypes = [i, d, d, i, d, P, i, P, l, P, P]
         lib.or_nbody_rows.argtypes = [i, d, d, i, d, i, P, l, P, P]
+        lib.or_field_eval.argtypes = [i, d, d, i, d, P, l, P, P, P]
         lib.or_lu_solve.argtypes = [l, P, i, P]
         lib.or_num_threads.argtypes = []
         _lib = lib
@@ -195,6 +196,20 @@ def matvec_rows(n_side: int, kappa: float, q, v, rows, x0: float = -1.0, x1: flo
     _check(st, "matvec_rows")
     res = out[..., 0] + 1j * out[..., 1]
     return res[:, 0] if squeeze else res
+
+
+def field_eval(n_side: int, kappa: float, psi, pts, x0: float = -1.0, x1: float = 1.0, p: int = 4):
+    """(u, psi_at) at the points pts (m x 2): the volume potential of the
+    interpolant of the grid values psi (Eq. 5, 7) and the interpolant itself
+    (zero outside the domain), the ingredients of E(x) (Section 6.1)."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    pv = np.ascontiguousarray(np.stack([psi.real, psi.imag], axis=-1))
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64))
+    m = pts.shape[0]
+    u = np.zeros((m, 2))
+    pa = np.zeros((m, 2))
+    _check(_load().or_field_eval(n_side, x0, x1, p, float(kappa), _ptr(pv), m, _ptr(pts), _ptr(u), _ptr(pa)), "field_eval")
+    return u[:, 0] + 1j * u[:, 1], pa[:, 0] + 1j * pa[:, 1]
 
 
 def nbody_rows(n_side: int, kappa: float, v, rows, x0: float = -1.0, x1: float = 1.0, p: int = 4) -> np.ndarray:

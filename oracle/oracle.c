@@ -21,7 +21,9 @@
  *   - rows of K, the matrix-vector product A v row by row, and a plain
  *     Gaussian-elimination LU solve of A psi = f (Eq. 12a);
  *   - the point N-body potential of Experiment 1 (Section 6.2) by direct
- *     summation over the same nodes.
+ *     summation over the same nodes;
+ *   - the interpolant psi(x) (Eq. 7) and its volume potential at arbitrary
+ *     points, the ingredients of the error function E(x) (Section 6.1).
  *
  * Quadrature (a reading: the paper names "adaptive Gauss quadrature" and
  * Boost's Hankel function, Section 2.3, but gives no rule): the reference
@@ -504,6 +506,65 @@ int or_matvec_rows(int n_side, double x0, double x1, int p, double kappa, const 
             cplx o = vi + kappa * kappa * q[i] * acc[k];
             out[2 * (r * nrhs + k)] = creal(o);
             out[2 * (r * nrhs + k) + 1] = cimag(o);
+        }
+    }
+    free(g.Qp);
+    return err;
+}
+
+/*
+ * Fields of a grid solution psi_vec at m arbitrary points x (Section 6.1's
+ * error function E(x)): psi(x) = sum_l Q^+(l,:) psi_vec^B b_l((x - alpha^B) /
+ * beta) on the leaf B containing x (Eq. 7; zero outside the domain), and the
+ * volume potential u(x) = sum_B sum_j' K(x, B, j') psi_vec^B_j' with the
+ * entries of Eq. 13 at the off-grid target x (the same quadrature as the
+ * rows of K).  psi complex interleaved (N), pts m x 2, u and psi_at m
+ * complex interleaved.
+ */
+int or_field_eval(int n_side, double x0, double x1, int p, double kappa, const double* psi, long m, const double* pts, double* u,
+                  double* psi_at)
+{
+    grid_ctx g;
+    int st = grid_init(&g, n_side, x0, x1, p, kappa);
+    if (st) { free(g.Qp); return st; }
+    int a[OR_MAX_NP], b[OR_MAX_NP];
+    or_basis_degrees(p, a, b);
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (long k = 0; k < m; k++) {
+        const double x = pts[2 * k], y = pts[2 * k + 1];
+        cplx blk[OR_MAX_P * OR_MAX_P];
+        cplx acc = 0.0;
+        for (long leaf = 0; leaf < g.nb * g.nb; leaf++) {
+            err |= leaf_entries(&g, x, y, leaf, blk);
+            for (int jp = 0; jp < g.n2; jp++) {
+                long j = leaf * g.n2 + jp;
+                acc += blk[jp] * (psi[2 * j] + I * psi[2 * j + 1]);
+            }
+        }
+        u[2 * k] = creal(acc);
+        u[2 * k + 1] = cimag(acc);
+        cplx pv = 0.0;
+        double ex = (x - x0) / (2.0 * g.beta), ey = (y - x0) / (2.0 * g.beta);
+        if (ex >= 0.0 && ey >= 0.0 && ex <= g.nb && ey <= g.nb) {
+            long bx = (long)floor(ex), by = (long)floor(ey);
+            if (bx > g.nb - 1) bx = g.nb - 1;
+            if (by > g.nb - 1) by = g.nb - 1;
+            long leaf = 0;
+            for (int q = 0; q < 31; q++) leaf |= (((bx >> q) & 1L) << (2 * q)) | (((by >> q) & 1L) << (2 * q + 1));
+            double tx = (x - (x0 + (2.0 * bx + 1.0) * g.beta)) / g.beta, ty = (y - (x0 + (2.0 * by + 1.0) * g.beta)) / g.beta;
+            for (int l = 0; l < g.np; l++) {
+                cplx cl = 0.0;
+                for (int jp = 0; jp < g.n2; jp++) {
+                    long j = leaf * g.n2 + jp;
+                    cl += g.Qp[l * g.n2 + jp] * (psi[2 * j] + I * psi[2 * j + 1]);
+                }
+                pv += cl * or_cheb_T(a[l], tx) * or_cheb_T(b[l], ty);
+            }
+        }
+        if (psi_at) {
+            psi_at[2 * k] = creal(pv);
+            psi_at[2 * k + 1] = cimag(pv);
         }
     }
     free(g.Qp);

@@ -164,6 +164,16 @@ int tree_nodes_dev(const dafmm_tree* tree, double* xy_dev, void* stream)
     });
 }
 
+int dafmm_field_eval(const dafmm_ops* ops, const double* psi, long m, const double* pts, double* u, double* psi_at, void* stream)
+{
+    return guarded([&] {
+        if (!ops || !psi || (m > 0 && (!pts || !u))) fail(DAFMM_EBADARG, "NULL argument");
+        if (m < 0 || m > 0x7fffffffL) fail(DAFMM_EBADARG, "point count out of range");
+        require_device();
+        field_eval(ops->tree->t, psi, m, pts, u, psi_at, (cudaStream_t)stream);
+    });
+}
+
 int dafmm_nbody_direct(const dafmm_tree* tree, const double* v, double* out, void* stream)
 {
     return guarded([&] {

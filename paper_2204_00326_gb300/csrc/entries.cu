@@ -70,10 +70,10 @@ void legendre_rule(int m, double* x, double* w)
     }
 }
 
-// acc[2l], acc[2l+1] += w * G(|y - t|) * b_l(y), G = (i/4)(J0 + i Y0)
-__device__ __forceinline__ void add_point(double yx, double yy, double tx, double ty, double kb, double w, double* acc)
+// acc[2l], acc[2l+1] += w * G(r) * b_l(y), G = (i/4)(J0 + i Y0), r = |y - t|
+// given by the rule (near the target y - t cancels in floating point)
+__device__ __forceinline__ void add_point(double yx, double yy, double r, double kb, double w, double* acc)
 {
-    double r = hypot(yx - tx, yy - ty);
     double z = kb * r;
     double gr = -0.25 * y0(z) * w;
     double gi = 0.25 * j0(z) * w;
@@ -89,6 +89,80 @@ __device__ __forceinline__ void add_point(double yx, double yy, double tx, doubl
             acc[2 * l + 1] += gi * bv;
             l++;
         }
+}
+
+// Quadrature points (y, weight, |y - t|) over the reference square [-1,1]^2
+// for a target t that may lie inside or near it: the square as the signed
+// sum of the four triangles (t, edge), each mapped to (u, s) with y = t + u
+// (h n + s |h| tau), Jacobian u h |h| and |y - t| = u |h| sqrt(1 + s^2); u
+// on geometric panels [2^-(k+1), 2^-k], s on panels graded away from the
+// foot of the perpendicular, 12-point Gauss-Legendre on every panel.  The
+// CTA's threads split the points; f is called for each point this thread
+// owns.
+template <class F>
+__device__ void near_rule(double tx, double ty, F&& f)
+{
+    // square [-1,1]^2, counter-clockwise vertices
+    const double vx[5] = {-1.0, 1.0, 1.0, -1.0, -1.0};
+    const double vy[5] = {-1.0, -1.0, 1.0, 1.0, -1.0};
+    for (int e = 0; e < 4; e++) {
+        const double ax = vx[e], ay = vy[e], bx = vx[e + 1], by = vy[e + 1];
+        const double len = hypot(bx - ax, by - ay);
+        const double tux = (bx - ax) / len, tuy = (by - ay) / len;  // tangent
+        const double nx = tuy, ny = -tux;                            // outward normal
+        const double h = (ax - tx) * nx + (ay - ty) * ny;            // signed distance
+        const double ah = fabs(h);
+        if (ah < 1e-13) continue;
+        const double fx = tx + h * nx, fy = ty + h * ny;             // foot
+        const double sa = ((ax - fx) * tux + (ay - fy) * tuy) / ah;
+        const double sb = ((bx - fx) * tux + (by - fy) * tuy) / ah;
+        // s panel breakpoints: sa, +-2^k (k = 0..40) and 0 inside (sa, sb), sb
+        // (targets off the grid may lie very close to an edge line, where |s|
+        // reaches 2 / |h|; grid targets never pass 2^10)
+        double bp[85];
+        int nbp = 0;
+        bp[nbp++] = sa;
+        {
+            double cand[83];
+            int nc = 0;
+            for (int k = 40; k >= 0; k--) cand[nc++] = -ldexp(1.0, k);
+            cand[nc++] = 0.0;
+            for (int k = 0; k <= 40; k++) cand[nc++] = ldexp(1.0, k);
+            for (int k = 0; k < nc; k++)
+                if (cand[k] > sa && cand[k] < sb) bp[nbp++] = cand[k];
+        }
+        bp[nbp++] = sb;
+        const int nsp = nbp - 1;
+        const int per_panel = kNearM * kNearM;
+        const int items = nsp * (kUPanels + 1) * per_panel;
+        for (int q = threadIdx.x; q < items; q += blockDim.x) {
+            int pt = q % per_panel;
+            int rest = q / per_panel;
+            int up = rest % (kUPanels + 1);
+            int sp = rest / (kUPanels + 1);
+            double u0 = (up == kUPanels) ? 0.0 : ldexp(1.0, -(up + 1));
+            double u1 = ldexp(1.0, -up);
+            double s0 = bp[sp], s1 = bp[sp + 1];
+            int iu = pt % kNearM, is = pt / kNearM;
+            double u = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * c_nx[iu];
+            double s = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * c_nx[is];
+            double w = 0.25 * (u1 - u0) * (s1 - s0) * c_nw[iu] * c_nw[is];
+            double yx = tx + u * (h * nx + s * ah * tux);
+            double yy = ty + u * (h * ny + s * ah * tuy);
+            f(yx, yy, w * u * h * ah, u * ah * sqrt(1.0 + s * s));
+        }
+    }
+}
+
+// The 16 x 16 tensor Gauss-Legendre points of the reference square (far
+// targets); the CTA's threads split them.
+template <class F>
+__device__ void far_rule(double tx, double ty, F&& f)
+{
+    for (int q = threadIdx.x; q < kFarM * kFarM; q += blockDim.x) {
+        const int a = q % kFarM, b = q / kFarM;
+        f(c_fx[a], c_fx[b], c_fw[a] * c_fw[b], hypot(c_fx[a] - tx, c_fx[b] - ty));
+    }
 }
 
 // Block-wide sum of the 20 accumulators of every thread; result in sh[0..19].
@@ -138,10 +212,7 @@ __global__ void far_table_kernel(int nb, double kb, double beta2, double2* tab)
     double acc[2 * kNp];
 #pragma unroll
     for (int k = 0; k < 2 * kNp; k++) acc[k] = 0;
-    for (int q = threadIdx.x; q < kFarM * kFarM; q += blockDim.x) {
-        int a = q % kFarM, b = q / kFarM;
-        add_point(c_fx[a], c_fx[b], tx, ty, kb, c_fw[a] * c_fw[b], acc);
-    }
+    far_rule(tx, ty, [&](double yx, double yy, double w, double r) { add_point(yx, yy, r, kb, w, acc); });
     block_reduce20(acc, sh);
     write_row(sh + 32 * 2 * kNp, beta2, tab + (off * 16 + ip) * 16);
 }
@@ -162,54 +233,7 @@ __global__ void near_table_kernel(int nb, double kb, double beta2, double2* tab)
 #pragma unroll
     for (int k = 0; k < 2 * kNp; k++) acc[k] = 0;
 
-    // square [-1,1]^2, counter-clockwise vertices
-    const double vx[5] = {-1.0, 1.0, 1.0, -1.0, -1.0};
-    const double vy[5] = {-1.0, -1.0, 1.0, 1.0, -1.0};
-    for (int e = 0; e < 4; e++) {
-        const double ax = vx[e], ay = vy[e], bx = vx[e + 1], by = vy[e + 1];
-        const double len = hypot(bx - ax, by - ay);
-        const double tux = (bx - ax) / len, tuy = (by - ay) / len;  // tangent
-        const double nx = tuy, ny = -tux;                            // outward normal
-        const double h = (ax - tx) * nx + (ay - ty) * ny;            // signed distance
-        const double ah = fabs(h);
-        if (ah < 1e-13) continue;
-        const double fx = tx + h * nx, fy = ty + h * ny;             // foot
-        const double sa = ((ax - fx) * tux + (ay - fy) * tuy) / ah;
-        const double sb = ((bx - fx) * tux + (by - fy) * tuy) / ah;
-        // s panel breakpoints: sa, +-2^k (k = 0..10) and 0 inside (sa, sb), sb
-        double bp[26];
-        int nbp = 0;
-        bp[nbp++] = sa;
-        {
-            double cand[23];
-            int nc = 0;
-            for (int k = 10; k >= 0; k--) cand[nc++] = -ldexp(1.0, k);
-            cand[nc++] = 0.0;
-            for (int k = 0; k <= 10; k++) cand[nc++] = ldexp(1.0, k);
-            for (int k = 0; k < nc; k++)
-                if (cand[k] > sa && cand[k] < sb) bp[nbp++] = cand[k];
-        }
-        bp[nbp++] = sb;
-        const int nsp = nbp - 1;
-        const int per_panel = kNearM * kNearM;
-        const int items = nsp * (kUPanels + 1) * per_panel;
-        for (int q = threadIdx.x; q < items; q += blockDim.x) {
-            int pt = q % per_panel;
-            int rest = q / per_panel;
-            int up = rest % (kUPanels + 1);
-            int sp = rest / (kUPanels + 1);
-            double u0 = (up == kUPanels) ? 0.0 : ldexp(1.0, -(up + 1));
-            double u1 = ldexp(1.0, -up);
-            double s0 = bp[sp], s1 = bp[sp + 1];
-            int iu = pt % kNearM, is = pt / kNearM;
-            double u = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * c_nx[iu];
-            double s = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * c_nx[is];
-            double w = 0.25 * (u1 - u0) * (s1 - s0) * c_nw[iu] * c_nw[is];
-            double yx = tx + u * (h * nx + s * ah * tux);
-            double yy = ty + u * (h * ny + s * ah * tuy);
-            add_point(yx, yy, tx, ty, kb, w * u * h * ah, acc);
-        }
-    }
+    near_rule(tx, ty, [&](double yx, double yy, double w, double r) { add_point(yx, yy, r, kb, w, acc); });
     block_reduce20(acc, sh);
     write_row(sh + 32 * 2 * kNp, beta2, tab + (off * 16 + ip) * 16);
 }
@@ -233,6 +257,137 @@ __global__ void point_table_kernel(int nb, double kb, double2* tab)
     const double tx = 2.0 * dx + c_z[ip & 3] - c_z[jp & 3], ty = 2.0 * dy + c_z[ip >> 2] - c_z[jp >> 2];
     const double z = kb * hypot(tx, ty);
     tab[e] = make_double2(-0.25 * y0(z), 0.25 * j0(z));
+}
+
+// ---------------------------------------------------------------------------
+// Field evaluation at arbitrary points (Section 6.1's error function E(x)):
+// the interpolant psi(x) = sum_l c_l b_l((x - alpha) / beta) of Eq. 7 on the
+// leaf containing x, c = Q^+ psi_vec (zero outside the domain), and the
+// volume potential u(x) = int_Omega G(x, y) psi(y) dy = beta^2 sum_B
+// int_[-1,1]^2 G(kappa beta |t_B - eta|) psi_B(eta) d eta, t_B = (x -
+// alpha_B) / beta, with the near rule for boxes within one box width of x
+// and the 16 x 16 rule for the others.
+
+// b_l(x, y), l < 10, in the library's order (total degree, then decreasing a).
+__device__ __forceinline__ void basis_eval(double x, double y, double* b)
+{
+    const double Tx[4] = {1.0, x, 2.0 * x * x - 1.0, x * (4.0 * x * x - 3.0)};
+    const double Ty[4] = {1.0, y, 2.0 * y * y - 1.0, y * (4.0 * y * y - 3.0)};
+    int l = 0;
+#pragma unroll
+    for (int d = 0; d < 4; d++)
+#pragma unroll
+        for (int a = d; a >= 0; a--) b[l++] = Tx[a] * Ty[d - a];
+}
+
+// c[leaf][l] = sum_j' Q^+_{l j'} psi[leaf 16 + j'] (Eq. 7's coefficients).
+__global__ void field_coef_kernel(long nleaf, const double2* __restrict__ psi, double2* __restrict__ coef)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= nleaf * kNp) return;
+    const long leaf = e / kNp;
+    const int l = (int)(e % kNp);
+    double re = 0, im = 0;
+    for (int jp = 0; jp < 16; jp++) {
+        const double2 v = psi[leaf * 16 + jp];
+        re += c_qp[l * 16 + jp] * v.x;
+        im += c_qp[l * 16 + jp] * v.y;
+    }
+    coef[e] = make_double2(re, im);
+}
+
+// Leaf (x, y) of Morton index m (x bit below y bit).
+__device__ __forceinline__ void leaf_xy(long m, int& lx, int& ly)
+{
+    lx = 0;
+    ly = 0;
+    for (int k = 0; k < 31; k++) {
+        lx |= (int)((m >> (2 * k)) & 1) << k;
+        ly |= (int)((m >> (2 * k + 1)) & 1) << k;
+    }
+}
+
+__device__ __forceinline__ long leaf_index(int lx, int ly)
+{
+    long m = 0;
+    for (int k = 0; k < 31; k++) m |= ((long)((lx >> k) & 1) << (2 * k)) | ((long)((ly >> k) & 1) << (2 * k + 1));
+    return m;
+}
+
+// One CTA per point.
+__global__ void field_eval_kernel(long m, const double2* __restrict__ pts, int nb, double x0, double beta, double kb,
+                                  const double2* __restrict__ coef, double2* __restrict__ u, double2* __restrict__ psi_at)
+{
+    __shared__ double sh[2 * 32];
+    const double2 X = pts[blockIdx.x];
+    double ar = 0.0, ai = 0.0;
+    const long nleaf = (long)nb * nb;
+    for (long leaf = 0; leaf < nleaf; leaf++) {
+        int lx, ly;
+        leaf_xy(leaf, lx, ly);
+        const double tx = (X.x - (x0 + (2.0 * lx + 1.0) * beta)) / beta;
+        const double ty = (X.y - (x0 + (2.0 * ly + 1.0) * beta)) / beta;
+        double cr[kNp], ci[kNp];
+#pragma unroll
+        for (int l = 0; l < kNp; l++) {
+            const double2 c = __ldg(&coef[leaf * kNp + l]);
+            cr[l] = c.x;
+            ci[l] = c.y;
+        }
+        auto f = [&](double yx, double yy, double w, double r) {
+            const double z = kb * r;
+            const double gr = -0.25 * y0(z) * w, gi = 0.25 * j0(z) * w;
+            double b[kNp];
+            basis_eval(yx, yy, b);
+            double pr = 0.0, pim = 0.0;
+#pragma unroll
+            for (int l = 0; l < kNp; l++) {
+                pr += cr[l] * b[l];
+                pim += ci[l] * b[l];
+            }
+            ar += gr * pr - gi * pim;
+            ai += gr * pim + gi * pr;
+        };
+        if (fmax(fabs(tx), fabs(ty)) < 3.0)
+            near_rule(tx, ty, f);
+        else
+            far_rule(tx, ty, f);
+    }
+    // block sum in a fixed order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_down_sync(0xffffffffu, ar, o);
+        ai += __shfl_down_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) {
+        sh[2 * warp] = ar;
+        sh[2 * warp + 1] = ai;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sr = 0, si = 0;
+        for (int w = 0; w < nw; w++) {
+            sr += sh[2 * w];
+            si += sh[2 * w + 1];
+        }
+        u[blockIdx.x] = make_double2(beta * beta * sr, beta * beta * si);
+        if (psi_at) {
+            const double ex = (X.x - x0) / (2.0 * beta), ey = (X.y - x0) / (2.0 * beta);
+            double2 pv = make_double2(0.0, 0.0);
+            if (ex >= 0.0 && ey >= 0.0 && ex <= nb && ey <= nb) {
+                const int lx = min((int)floor(ex), nb - 1), ly = min((int)floor(ey), nb - 1);
+                const long leaf = leaf_index(lx, ly);
+                double b[kNp];
+                basis_eval((X.x - (x0 + (2.0 * lx + 1.0) * beta)) / beta, (X.y - (x0 + (2.0 * ly + 1.0) * beta)) / beta, b);
+                for (int l = 0; l < kNp; l++) {
+                    const double2 c = coef[leaf * kNp + l];
+                    pv.x += c.x * b[l];
+                    pv.y += c.y * b[l];
+                }
+            }
+            psi_at[blockIdx.x] = pv;
+        }
+    }
 }
 
 #define CK(x)                                                                                     \
@@ -309,6 +464,27 @@ double build_entry_table(const Tree& t, EntryTable& out, void* stream_)
     out.lx = &t.leaf_x;
     out.ly = &t.leaf_y;
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void field_eval(const Tree& t, const double* psi, long m, const double* pts, double* u, double* psi_at, cudaStream_t stream)
+{
+    cudaGetLastError();
+    if (t.p != 4) fail(DAFMM_EBADARG, "field evaluation supports p = 4");
+    const long nleaf = (long)t.nb * t.nb;
+    double2* coef = nullptr;
+    if (cudaMallocAsync((void**)&coef, sizeof(double2) * nleaf * kNp, stream) != cudaSuccess) {
+        cudaGetLastError();
+        fail(DAFMM_ENOMEM, "device allocation of the interpolation coefficients failed");
+    }
+    field_coef_kernel<<<(unsigned)((nleaf * kNp + 255) / 256), 256, 0, stream>>>(nleaf, (const double2*)psi, coef);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && m > 0) {
+        field_eval_kernel<<<(unsigned)m, 256, 0, stream>>>(m, (const double2*)pts, t.nb, t.x0, t.beta, t.prm.kappa * t.beta, coef,
+                                                           (double2*)u, (double2*)psi_at);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(coef, stream);
+    if (e != cudaSuccess) fail(DAFMM_ECUDA, std::string("field evaluation kernels: ") + cudaGetErrorString(e));
 }
 
 }  // namespace dafmm

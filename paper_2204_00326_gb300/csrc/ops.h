@@ -198,6 +198,8 @@ double* unet_scalars(dafmm_unet* u);  // 2 device doubles owned by the network
 void node_coords(const Tree& t, double* xy);
 void node_coords_dev(const Tree& t, double* xy_dev, cudaStream_t s);
 void nbody_direct(const Tree& t, const double* v, double* out, cudaStream_t s);
+// psi(x_k) (Eq. 7) and u(x_k) = V[psi](x_k) at m points (entries.cu)
+void field_eval(const Tree& t, const double* psi, long m, const double* pts, double* u, double* psi_at, cudaStream_t s);
 
 // Kernels one application launches.
 int launches_per_call(const Tree& t, const OpsDev& d, int precision);

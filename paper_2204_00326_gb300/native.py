@@ -162,6 +162,7 @@ _sig = {
     "dafmm_set_batched_kernel": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_nbody_direct": ([_P, _P, _P, _P], ctypes.c_int),
     "tree_nodes_dev": ([_P, _P, _P], ctypes.c_int),
+    "dafmm_field_eval": ([_P, _P, ctypes.c_long, _P, _P, _P, _P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_potential": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -307,6 +308,21 @@ def dafmm_matvec_noalloc(ops: int, v, out, precision: int = DAFMM_FP64, stream=N
     if v.dim() != 1 or out.shape != v.shape:
         raise ValueError("one right-hand side: v and out are (N,) vectors")
     _check(lib.dafmm_matvec_noalloc(ops, _dptr(v, "complex128"), _dptr(out, "complex128"), precision, _stream_ptr(stream)))
+
+
+def dafmm_field_eval(ops: int, psi, pts, want_psi: bool = True, stream=None):
+    """(u, psi_at): the volume potential V[psi](x) and the interpolant psi(x)
+    (Eq. 7) at the points pts ((m, 2) float64 CUDA tensor)."""
+    import torch
+
+    if pts.dim() != 2 or pts.shape[1] != 2:
+        raise ValueError("pts is an (m, 2) tensor")
+    m = pts.shape[0]
+    u = torch.empty(m, dtype=torch.complex128, device=pts.device)
+    pa = torch.empty_like(u) if want_psi else None
+    _check(lib.dafmm_field_eval(ops, _dptr(psi, "complex128"), m, _dptr(pts.contiguous(), "float64"), _dptr(u, "complex128"),
+                                _dptr(pa, "complex128") if pa is not None else None, _stream_ptr(stream)))
+    return u, pa
 
 
 def dafmm_nbody_direct(tree: int, v, out, stream=None) -> None:

@@ -271,3 +271,45 @@ def test_nbody_matrix_is_symmetric_with_zero_diagonal():
         eb[b] = 1.0
         assert O.nbody_rows(n, kappa, eb, [a])[0] == O.nbody_rows(n, kappa, ea, [b])[0]
         assert O.nbody_rows(n, kappa, ea, [a])[0] == 0.0
+
+
+def test_field_eval_at_the_nodes_equals_rows_of_K():
+    """At a grid node the off-grid field is the row of K applied to psi."""
+    n, kappa = 16, 8.0
+    xy = O.grid_nodes(n)
+    rng = np.random.default_rng(5)
+    psi = rng.standard_normal(n * n) + 1j * rng.standard_normal(n * n)
+    rows = np.array([0, 37, 200, 255])
+    u, _ = O.field_eval(n, kappa, psi, xy[rows])
+    ref = O.K_rows(n, kappa, rows) @ psi
+    assert np.abs(u - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_field_eval_interpolant_reproduces_polynomials():
+    """Eq. 7's interpolant is exact for a global polynomial of total degree
+    < p, at any point of the domain, and zero outside it."""
+    n = 16
+    xy = O.grid_nodes(n)
+
+    def g(p):
+        x, y = p[:, 0], p[:, 1]
+        return 1.0 + 2.0 * x - 0.5 * y + x * y - 1.5 * y ** 2 + 0.7 * x ** 3 - 0.2 * x * y ** 2
+
+    pts = np.random.default_rng(6).uniform(-1, 1, size=(50, 2))
+    _, pa = O.field_eval(n, 3.0, g(xy).astype(complex), np.vstack([pts, [[1.5, 0.0], [0.0, -1.2]]]))
+    assert np.abs(pa[:50] - g(pts)).max() < 1e-12
+    assert pa[50] == 0 and pa[51] == 0
+
+
+def test_field_eval_manufactured_solution_off_the_grid():
+    """psi = -(Laplacian + kappa^2) phi gives V[psi] = phi exactly; at points
+    off the grid the error of the discretised potential falls at order ~p."""
+    kappa = 8.0
+    phi, psi = _manufactured(kappa)
+    pts = np.random.default_rng(7).uniform(-0.9, 0.9, size=(12, 2))
+    errs = []
+    for n in (16, 32):
+        u, _ = O.field_eval(n, kappa, psi(O.grid_nodes(n)).astype(complex), pts)
+        errs.append(np.linalg.norm(u - phi(pts)) / np.linalg.norm(phi(pts)))
+    assert errs[1] < 5e-3
+    assert errs[0] / errs[1] > 8.0

@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-residual solves")
     ap.add_argument("--no-nbody", action="store_true", help="skip Experiment 1's N-body measurement")
+    ap.add_argument("--no-mixed-batch", action="store_true", help="skip the mixed-size batch of problems")
     ap.add_argument("--no-batched-solve", action="store_true",
                     help="skip the 64-plane-wave solve on the 256 x 256, kappa = 80 disc workload")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides of the batched measurement (1 = skip)")
@@ -326,6 +327,53 @@ def batched_solve(N, DafmmOperator, nrhs=64, rank=15, singles=4):
     return out
 
 
+def mixed_size_batch(N, DafmmOperator, count=8, sizes=(64, 128, 256), nrhs=8, reps=10):
+    """The mixed-size batch (kappa = 0.3 sqrt(N), bump or disc contrasts, 8
+    plane waves each): every problem's several-right-hand-side passes tuned
+    (dafmm_tune_batched, choice recorded), then the whole batch applied in
+    one captured graph (dafmm_batch_matvec), against the same applications
+    launched one problem after another.  Grids up to 256^2: a 1024^2 problem
+    alone holds tens of GB of operators and needs a long host setup."""
+    import torch
+
+    ws = W.mixed_size_batch(count=count, sizes=sizes, seed=5, nrhs=nrhs)
+    t0 = time.perf_counter()
+    ops = [DafmmOperator(w.n_side, w.kappa, lambda xy, w=w: W.contrast(w, xy)) for w in ws]
+    setup = time.perf_counter() - t0
+    vs = [torch.as_tensor(W.plane_waves(w.kappa, op.xy, nrhs) * (-w.kappa ** 2 * op.q)[:, None], device="cuda").contiguous()
+          for w, op in zip(ws, ops)]
+    outs = [torch.empty_like(v) for v in vs]
+    total = sum(w.N for w in ws) * nrhs
+    out = {"problems": [w.name for w in ws], "nrhs": nrhs, "unknowns_x_rhs": total, "setup_s": setup,
+           "sizes_note": "grids drawn from 64^2, 128^2, 256^2"}
+    out["tuning"] = {w.name: N.dafmm_tune_batched(op.ops, nrhs, N.DAFMM_MIXED) for w, op in zip(ws, ops)}
+    b = N.Batch([op.ops for op in ops])
+    for name, prec in (("mixed", N.DAFMM_MIXED), ("fp64", N.DAFMM_FP64)):
+        for _ in range(3):
+            b.matvec(vs, outs, prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.matvec(vs, outs, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        e0.record()
+        for _ in range(reps):
+            for op, v, o in zip(ops, vs, outs):
+                op.matvec(v, o, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_seq = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_batch": ms, "munknowns_rhs_per_s": total / (ms * 1e-3) / 1e6,
+                     "ms_one_problem_after_another": ms_seq}
+    b.close()
+    for op in ops:
+        op.close()
+    return out
+
+
 def experiment1(N, DafmmOperator, reps=10):
     """Experiment 1 (Section 6.2): the point N-body potential of random
     charges at the 256 x 256 Chebyshev nodes (N = 65536, kappa = 50) by the
@@ -569,6 +617,9 @@ def main():
     exp1 = None
     if not a.no_nbody and world == 1:
         exp1 = experiment1(N, DafmmOperator)
+    mbatch = None
+    if not a.no_mixed_batch and world == 1:
+        mbatch = mixed_size_batch(N, DafmmOperator)
 
     clk.__exit__(None, None, None)
 
@@ -595,6 +646,7 @@ def main():
         "time_to_residual": ttr,
         "time_to_residual_batched": ttr_b,
         "experiment1_nbody": exp1,
+        "mixed_size_batch": mbatch,
         "setup_s": {"total": setup_s, "entry_table": st.setup_seconds_table, "nca": st.setup_seconds_nca},
         "operator": {"bytes_fp32": st.operator_bytes_fp32, "bytes_fp64": st.operator_bytes_fp64,
                      "cmacs_per_rhs": st.cmacs_per_rhs},

@@ -478,6 +478,60 @@ int dafmm_field_eval(const dafmm_ops* ops, const double* psi_dev, long m, const 
  */
 int dafmm_nbody_direct(const dafmm_tree* tree, const double* v_dev, double* out_dev, void* stream);
 
+/*
+ * Tuning of the several-right-hand-side passes (see dafmm_tune_batched).
+ * kernel: 1 CUDA cores, 2 tensor cores; ctas_per_sm: cap on the CTAs per SM
+ * of the CUDA-core pass grids (0: as many as fit).
+ */
+typedef struct dafmm_tuning {
+    int nrhs;              /* right-hand sides it was tuned for */
+    int precision;         /* DAFMM_FP64 or DAFMM_MIXED */
+    int kernel;            /* the choice */
+    int ctas_per_sm;       /* the choice */
+    double best_ms;        /* time of one application with the choice */
+    int ncand;             /* candidates timed */
+    int cand_kernel[16];
+    int cand_ctas[16];
+    double cand_ms[16];    /* each candidate's time of one application */
+    int reserved[8];
+} dafmm_tuning;
+
+/*
+ * dafmm_tune_batched -- time the candidate configurations of the tree passes
+ * of an application with nrhs (2..64) right-hand sides in the given
+ * precision: the CUDA-core kernel with 0 (all that fit), 1, 2 and 4 CTAs per
+ * SM, and in DAFMM_MIXED the tensor-core kernel; each candidate runs two
+ * untimed and five timed applications (CUDA events) on a private stream with
+ * a fixed input.  The fastest is kept on the handle (as by
+ * dafmm_set_batched_kernel and dafmm_set_batched_grid) and recorded in *out
+ * with every candidate's time.  Results do not depend on the choice beyond
+ * rounding.  Allocates two N x nrhs vectors for the call; synchronises.
+ * Errors: DAFMM_EBADARG, DAFMM_ENOMEM, DAFMM_ECUDA.
+ */
+int dafmm_tune_batched(dafmm_ops* ops, int nrhs, int precision, dafmm_tuning* out);
+
+/* Cap the CTAs per SM of the CUDA-core several-right-hand-side pass grids
+ * (0: as many as fit, else 1..32).  Cached application graphs are dropped
+ * when it changes.  Errors: DAFMM_EBADARG. */
+int dafmm_set_batched_grid(dafmm_ops* ops, int ctas_per_sm);
+
+/*
+ * Several problems (operators of different sizes, each with its own tree)
+ * applied together.  dafmm_batch_matvec computes out[i] = A_i v[i] for every
+ * problem i, nrhs right-hand sides each, in one CUDA graph: every problem's
+ * kernels on a stream of its own forked from the graph's start, so the
+ * problems' kernels overlap; the graph is captured on the first call for a
+ * given (nrhs, precision, pointers) and replayed by one cudaGraphLaunch
+ * after that (at most four such sets are kept).  v_dev, out_dev: host arrays
+ * of n device pointers, each vector N_i x nrhs complex128.  The handles must
+ * outlive the batch and must not be used concurrently elsewhere.
+ * Errors: DAFMM_EBADARG, DAFMM_ENOMEM, DAFMM_ECUDA.
+ */
+typedef struct dafmm_batch dafmm_batch;
+int dafmm_batch_create(int n, dafmm_ops* const* ops, dafmm_batch** out);
+int dafmm_batch_matvec(dafmm_batch* batch, int nrhs, const double* const* v_dev, double* const* out_dev, int precision, void* stream);
+int dafmm_batch_destroy(dafmm_batch* batch);
+
 /* Realised ranks, operator bytes and work of one application. */
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats);
 

@@ -2580,6 +2580,7 @@ void launch_batched_mr(const OpsDev& d, const Group& g, const GroupArgs<T>& ga, 
     CK(cudaFuncSetAttribute(stream_batched_kernel<T, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_batched_kernel<T, MR>, threads, smem));
+    if (d.batched_cps > 0) per_sm = std::min(per_sm, d.batched_cps);  // tuned grid
     per_sm = std::max(per_sm, 1);
     int kpc = 1;
     if (g.nch > 0) {
@@ -2852,6 +2853,19 @@ void set_batched_kernel(OpsDev& d, int mode)
     if (mode == d.batched_kernel) return;
     d.batched_kernel = mode;
     // captured applications hold the previous kernels
+    for (auto& row : d.gc)
+        for (auto& G : row) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.graph) cudaGraphDestroy(G.graph);
+            G = GraphCache();
+        }
+}
+
+void set_batched_grid(OpsDev& d, int cps)
+{
+    if (cps < 0 || cps > 32) fail(DAFMM_EBADARG, "CTAs per SM must lie in 0..32");
+    if (cps == d.batched_cps) return;
+    d.batched_cps = cps;
     for (auto& row : d.gc)
         for (auto& G : row) {
             if (G.exec) cudaGraphExecDestroy(G.exec);

@@ -445,6 +445,57 @@ int dafmm_set_batched_kernel(dafmm_ops* ops, int mode)
     });
 }
 
+int dafmm_set_batched_grid(dafmm_ops* ops, int ctas_per_sm)
+{
+    return guarded([&] {
+        if (!ops) fail(DAFMM_EBADARG, "NULL argument");
+        set_batched_grid(ops->dev, ctas_per_sm);
+    });
+}
+
+int dafmm_tune_batched(dafmm_ops* ops, int nrhs, int precision, dafmm_tuning* out)
+{
+    return guarded([&] {
+        if (!ops || !out) fail(DAFMM_EBADARG, "NULL argument");
+        if (nrhs < 2 || nrhs > 64) fail(DAFMM_EBADARG, "nrhs must lie in 2..64");
+        if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+        require_device();
+        std::memset(out, 0, sizeof(*out));
+        tune_batched(ops, nrhs, precision, *out);
+    });
+}
+
+int dafmm_batch_create(int n, dafmm_ops* const* ops, dafmm_batch** out)
+{
+    return guarded([&] {
+        if (!ops || !out || n < 1) fail(DAFMM_EBADARG, "NULL argument or no problems");
+        *out = nullptr;
+        for (int i = 0; i < n; i++)
+            if (!ops[i]) fail(DAFMM_EBADARG, "NULL operator in the batch");
+        require_device();
+        *out = batch_new(n, ops);
+    });
+}
+
+int dafmm_batch_matvec(dafmm_batch* b, int nrhs, const double* const* v, double* const* out, int precision, void* stream)
+{
+    return guarded([&] {
+        if (!b || !v || !out) fail(DAFMM_EBADARG, "NULL argument");
+        if (nrhs < 1 || nrhs > 64) fail(DAFMM_EBADARG, "nrhs must lie in 1..64");
+        if (precision != DAFMM_FP64 && precision != DAFMM_MIXED) fail(DAFMM_EBADARG, "unknown precision");
+        const size_t n = batch_size(b);
+        for (size_t i = 0; i < n; i++)
+            if (!v[i] || !out[i] || v[i] == out[i]) fail(DAFMM_EBADARG, "NULL or aliased vector in the batch");
+        batch_matvec(b, nrhs, v, out, precision, (cudaStream_t)stream);
+    });
+}
+
+int dafmm_batch_destroy(dafmm_batch* b)
+{
+    batch_free(b);
+    return DAFMM_OK;
+}
+
 int dafmm_set_contrast(dafmm_ops* ops, const double* q_dev, void* stream)
 {
     return guarded([&] {

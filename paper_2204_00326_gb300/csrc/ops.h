@@ -135,6 +135,7 @@ struct OpsDev {
     GmresWork* gw = nullptr;
     GmresMany* gm = nullptr;
     int batched_kernel = 0;     // several right-hand sides, complex64: 0 automatic, 1 CUDA cores, 2 tensor cores
+    int batched_cps = 0;        // several right-hand sides, CUDA cores: CTAs per SM of the pass grids (0: as many as fit)
 };
 
 // Allocate and upload; frees host block storage as it goes.
@@ -142,6 +143,7 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d);
 void free_ops(OpsDev& d);
 void profile_enable(OpsDev& d, bool on);
 void set_batched_kernel(OpsDev& d, int mode);
+void set_batched_grid(OpsDev& d, int ctas_per_sm);
 void profile_read(OpsDev& d, dafmm_profile_t& p);
 // Make sure scratch holds nrhs right-hand sides.
 void ensure_scratch(const Tree& t, OpsDev& d, int nrhs);
@@ -200,6 +202,13 @@ void node_coords_dev(const Tree& t, double* xy_dev, cudaStream_t s);
 void nbody_direct(const Tree& t, const double* v, double* out, cudaStream_t s);
 // psi(x_k) (Eq. 7) and u(x_k) = V[psi](x_k) at m points (entries.cu)
 void field_eval(const Tree& t, const double* psi, long m, const double* pts, double* u, double* psi_at, cudaStream_t s);
+
+// Several problems in one captured application; the tuner (batch.cpp).
+dafmm_batch* batch_new(int n, dafmm_ops* const* ops);
+void batch_free(dafmm_batch* b);
+size_t batch_size(const dafmm_batch* b);
+void batch_matvec(dafmm_batch* b, int nrhs, const double* const* v, double* const* out, int precision, cudaStream_t s);
+void tune_batched(dafmm_ops* ops, int nrhs, int precision, dafmm_tuning& r);
 
 // Kernels one application launches.
 int launches_per_call(const Tree& t, const OpsDev& d, int precision);

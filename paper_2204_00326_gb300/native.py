@@ -49,6 +49,21 @@ class dafmm_params(ctypes.Structure):
     ]
 
 
+class dafmm_tuning(ctypes.Structure):
+    _fields_ = [
+        ("nrhs", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("best_ms", ctypes.c_double),
+        ("ncand", ctypes.c_int),
+        ("cand_kernel", ctypes.c_int * 16),
+        ("cand_ctas", ctypes.c_int * 16),
+        ("cand_ms", ctypes.c_double * 16),
+        ("reserved", ctypes.c_int * 8),
+    ]
+
+
 class dafmm_tree_info(ctypes.Structure):
     _fields_ = [
         ("N", ctypes.c_long),
@@ -163,6 +178,11 @@ _sig = {
     "dafmm_nbody_direct": ([_P, _P, _P, _P], ctypes.c_int),
     "tree_nodes_dev": ([_P, _P, _P], ctypes.c_int),
     "dafmm_field_eval": ([_P, _P, ctypes.c_long, _P, _P, _P, _P], ctypes.c_int),
+    "dafmm_tune_batched": ([_P, ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
+    "dafmm_set_batched_grid": ([_P, ctypes.c_int], ctypes.c_int),
+    "dafmm_batch_create": ([ctypes.c_int, _P, _P], ctypes.c_int),
+    "dafmm_batch_matvec": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "dafmm_batch_destroy": ([_P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_potential": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -330,6 +350,55 @@ def dafmm_nbody_direct(tree: int, v, out, stream=None) -> None:
     if v.dim() != 1 or out.shape != v.shape:
         raise ValueError("v and out are (N,) vectors")
     _check(lib.dafmm_nbody_direct(tree, _dptr(v, "complex128"), _dptr(out, "complex128"), _stream_ptr(stream)))
+
+
+def dafmm_tune_batched(ops: int, nrhs: int, precision: int) -> dict:
+    """Time the several-right-hand-side pass configurations, keep the fastest;
+    returns the choice and every candidate's time (ms per application)."""
+    r = dafmm_tuning()
+    _check(lib.dafmm_tune_batched(ops, int(nrhs), int(precision), ctypes.byref(r)))
+    kinds = {1: "cuda_cores", 2: "tensor_cores"}
+    return {"nrhs": r.nrhs, "precision": "fp64" if r.precision == DAFMM_FP64 else "mixed", "kernel": kinds[r.kernel],
+            "ctas_per_sm": r.ctas_per_sm, "best_ms": r.best_ms,
+            "candidates": [{"kernel": kinds[r.cand_kernel[k]], "ctas_per_sm": r.cand_ctas[k], "ms": r.cand_ms[k]} for k in range(r.ncand)]}
+
+
+def dafmm_set_batched_grid(ops: int, ctas_per_sm: int) -> None:
+    _check(lib.dafmm_set_batched_grid(ops, int(ctas_per_sm)))
+
+
+class Batch:
+    """Several operators applied together in one captured CUDA graph
+    (dafmm_batch_create / dafmm_batch_matvec)."""
+
+    def __init__(self, ops_handles):
+        self.n = len(ops_handles)
+        arr = (_P * self.n)(*ops_handles)
+        h = _P()
+        _check(lib.dafmm_batch_create(self.n, arr, ctypes.byref(h)))
+        self.h = h.value
+
+    def matvec(self, vs, outs, precision: int = DAFMM_FP64, stream=None) -> None:
+        if len(vs) != self.n or len(outs) != self.n:
+            raise ValueError("one input and one output per problem")
+        nrhs = 1 if vs[0].dim() == 1 else vs[0].shape[1]
+        for v, o in zip(vs, outs):
+            if o.shape != v.shape or (1 if v.dim() == 1 else v.shape[1]) != nrhs:
+                raise ValueError("every problem takes the same number of right-hand sides")
+        va = (_P * self.n)(*[_dptr(v, "complex128") for v in vs])
+        oa = (_P * self.n)(*[_dptr(o, "complex128") for o in outs])
+        _check(lib.dafmm_batch_matvec(self.h, nrhs, va, oa, precision, _stream_ptr(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib.dafmm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 BATCHED_AUTO, BATCHED_CUDA_CORES, BATCHED_TENSOR_CORES = 0, 1, 2

@@ -51,6 +51,22 @@ NBODY256_K50 = Workload("nbody256_k50", 256, 50.0, "zero")
 WORKLOADS = {w.name: w for w in (GRID32_K8, GRID128_K40, GRID256_K80, GRID512_K160)}
 
 
+def mixed_size_batch(count: int = 16, sizes=(64, 128, 256, 512, 1024), seed: int = 5, nrhs: int = 8) -> list:
+    """The mixed-size batch of problems: grids drawn from `sizes`, kappa =
+    0.3 sqrt(N) (the same points per wavelength at every size), contrast a
+    Gaussian-bump mixture (as in the 128^2 workload, 4 bumps) or the disc,
+    each with probability 1/2, all from one seed; nrhs plane waves each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(count):
+        n = int(sizes[rng.integers(len(sizes))])
+        if rng.random() < 0.5:
+            out.append(Workload(f"batch{k}_grid{n}_bumps4", n, 0.3 * n, "bumps", nbumps=4, seed=seed * 1000 + k, nrhs=nrhs))
+        else:
+            out.append(Workload(f"batch{k}_grid{n}_disc", n, 0.3 * n, "disc", nrhs=nrhs))
+    return out
+
+
 def contrast(w: Workload, xy: np.ndarray) -> np.ndarray:
     """q(x) at the points xy (N x 2)."""
     x, y = xy[:, 0], xy[:, 1]

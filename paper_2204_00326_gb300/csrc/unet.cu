@@ -159,12 +159,15 @@ __global__ void __launch_bounds__(kThreads) wgrad_kernel(int B, int H, int W, in
         }
         __syncthreads();
     }
-    if (ci0 + c < cin && co0 + co < cout)
+    // this block's partial of its weights, slot blockIdx.y (summed in slot order by sum_slots_kernel)
+    if (ci0 + c < cin && co0 + co < cout) {
+        const size_t nw = (size_t)K * K * cin * cout;
 #pragma unroll
-        for (int k = 0; k < K * K; k++) atomicAdd(&dw[((size_t)k * cin + ci0 + c) * cout + co0 + co], acc[k]);
+        for (int k = 0; k < K * K; k++) dw[(size_t)blockIdx.y * nw + ((size_t)k * cin + ci0 + c) * cout + co0 + co] = acc[k];
+    }
 }
 
-// db[co] += sum_p d[p][co]
+// The partial of sum_p d[p][co] over this block's pixels, slot blockIdx.x.
 __global__ void bgrad_kernel(long npix, int cout, const float* __restrict__ d, float* __restrict__ db)
 {
     __shared__ float s[8][33];
@@ -176,8 +179,19 @@ __global__ void bgrad_kernel(long npix, int cout, const float* __restrict__ d, f
     __syncthreads();
     if (threadIdx.y == 0 && co < cout) {
         for (int k = 1; k < 8; k++) a += s[k][threadIdx.x];
-        atomicAdd(&db[co], a);
+        db[(size_t)blockIdx.x * cout + co] = a;
     }
+}
+
+// out[i] += sum over slots g < G of part[g n + i], in slot order (gradients
+// that do not depend on timing, so training is reproducible run to run).
+__global__ void sum_slots_kernel(long n, int G, const float* __restrict__ part, float* __restrict__ out)
+{
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a = 0.f;
+    for (int g = 0; g < G; g++) a += part[(size_t)g * n + i];
+    out[i] += a;
 }
 
 // d[p][c] = g[p, goff + c] * (y[p, yoff + c] > 0): the gradient before a ReLU
@@ -388,6 +402,9 @@ struct UnetConv {
     long w_off, b_off;  // in the flat parameter array: weights [K][K][cin][cout], then bias [cout]
 };
 
+constexpr int kWSlots = 32;    // pixel-tile slots of a weight-gradient reduction
+constexpr int kBSlots = 1024;  // pixel blocks of a bias-gradient reduction
+
 struct UnetAct {
     int B = 0, H = 0, W = 0;
     std::vector<void*> mem;  // every allocation, freed together
@@ -400,6 +417,8 @@ struct UnetAct {
     float* gout = nullptr;  // [pixels][out_ch]
     float* dpre = nullptr;  // scratch: gradient before an activation
     bf16* wflip = nullptr;  // scratch: flipped kernel
+    float* wpart = nullptr;  // scratch: per-slot partial weight gradients of one convolution
+    float* bpart = nullptr;  // scratch: per-block partial bias gradients
     size_t grad_bytes = 0;  // of the FP32 gradient block (zeroed per backward pass)
     float* grad_block = nullptr;
 };
@@ -530,6 +549,10 @@ void act_ensure(dafmm_unet* u, int B, int H, int W)
     dpre = std::max(dpre, px(0) * (size_t)std::max(u->prm.out_ch, u->prm.in_ch));
     a.dpre = act_alloc<float>(a, dpre);
     a.wflip = act_alloc<bf16>(a, wf);
+    size_t cmax = 1;
+    for (const UnetConv& c : u->convs) cmax = std::max(cmax, (size_t)c.cout);
+    a.wpart = act_alloc<float>(a, wf * kWSlots);
+    a.bpart = act_alloc<float>(a, cmax * kBSlots);
 }
 
 template <typename Tin, typename Tout>
@@ -554,15 +577,19 @@ void wgrad(dafmm_unet* u, int idx, int B, int H, int W, const Tin* in, int is, i
 {
     const UnetConv& c = u->convs[idx];
     const int ntiles = B * ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
-    const int per = std::max(1, ntiles / 64);
-    dim3 grid((unsigned)(((c.cin + kCI - 1) / kCI) * ((c.cout + kTC - 1) / kTC)), (unsigned)((ntiles + per - 1) / per));
+    const int per = std::max(1, (ntiles + kWSlots - 1) / kWSlots);
+    const int G = (ntiles + per - 1) / per;  // slots, at most kWSlots
+    const long nw = (long)c.K * c.K * c.cin * c.cout;
+    dim3 grid((unsigned)(((c.cin + kCI - 1) / kCI) * ((c.cout + kTC - 1) / kTC)), (unsigned)G);
     if (c.K == 3)
-        wgrad_kernel<3, Tin><<<grid, kThreads, 0, s>>>(B, H, W, c.cin, c.cout, in, is, ioff, d, u->grad + c.w_off, per);
+        wgrad_kernel<3, Tin><<<grid, kThreads, 0, s>>>(B, H, W, c.cin, c.cout, in, is, ioff, d, u->act.wpart, per);
     else
-        wgrad_kernel<1, Tin><<<grid, kThreads, 0, s>>>(B, H, W, c.cin, c.cout, in, is, ioff, d, u->grad + c.w_off, per);
+        wgrad_kernel<1, Tin><<<grid, kThreads, 0, s>>>(B, H, W, c.cin, c.cout, in, is, ioff, d, u->act.wpart, per);
+    sum_slots_kernel<<<blocks(nw), 256, 0, s>>>(nw, G, u->act.wpart, u->grad + c.w_off);
     const long npix = (long)B * H * W;
-    bgrad_kernel<<<dim3((unsigned)std::min<long>(1024, (npix + 7) / 8), (unsigned)((c.cout + 31) / 32)), dim3(32, 8), 0, s>>>(
-        npix, c.cout, d, u->grad + c.b_off);
+    const int nbb = (int)std::min<long>(kBSlots, (npix + 7) / 8);
+    bgrad_kernel<<<dim3((unsigned)nbb, (unsigned)((c.cout + 31) / 32)), dim3(32, 8), 0, s>>>(npix, c.cout, d, u->act.bpart);
+    sum_slots_kernel<<<blocks(c.cout), 256, 0, s>>>(c.cout, nbb, u->act.bpart, u->grad + c.b_off);
     UCK(cudaGetLastError());
 }
 

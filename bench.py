@@ -457,11 +457,20 @@ def main():
     stream = torch.cuda.current_stream()
     v = torch.as_tensor(W.random_vector(w.N, 1, seed=1 + rank)[:, 0], device="cuda")
     out = torch.empty_like(v)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # L2 flush between timed steps: a read of 256 MiB (twice the L2) evicts every
+    # line the previous step touched.  A write of the buffer would do the same but
+    # leave up to 129 MB of dirty lines, whose write-back the next timed kernel
+    # would pay (measured: far field 102 us after a write, 96.5 us after a read,
+    # 94.6 us without any flush; the operators alone, 266 MB, exceed the L2).
+    flush_buf = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush_sink = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        torch.sum(flush_buf, out=flush_sink)
 
     def timed(prec, steps, profile):
         for _ in range(a.warmup):
-            flush.zero_()
+            flush_l2()
             op.matvec(v, out, prec)
         torch.cuda.synchronize()
         barrier()
@@ -470,7 +479,7 @@ def main():
             N.dafmm_profile(op.ops, True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for e0, e1 in evs:
-            flush.zero_()  # L2 flush between timed steps, outside the events
+            flush_l2()  # L2 flush between timed steps, outside the events
             e0.record(stream)
             op.matvec(v, out, prec)
             e1.record(stream)
@@ -546,12 +555,12 @@ def main():
         batched = {"nrhs": a.nrhs}
         for name, prec in (("mixed", N.DAFMM_MIXED), ("fp64", N.DAFMM_FP64)):
             for _ in range(a.warmup):
-                flush.zero_()
+                flush_l2()
                 op.matvec(Vb, Yb, prec)
             torch.cuda.synchronize()
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
             for e0b, e1b in evs:
-                flush.zero_()
+                flush_l2()
                 e0b.record(stream)
                 op.matvec(Vb, Yb, prec)
                 e1b.record(stream)
@@ -564,12 +573,12 @@ def main():
         # the same application with the tree passes on the tensor cores (opt-in kernel)
         N.dafmm_set_batched_kernel(op.ops, N.BATCHED_TENSOR_CORES)
         for _ in range(a.warmup):
-            flush.zero_()
+            flush_l2()
             op.matvec(Vb, Yb, N.DAFMM_MIXED)
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
         for e0b, e1b in evs:
-            flush.zero_()
+            flush_l2()
             e0b.record(stream)
             op.matvec(Vb, Yb, N.DAFMM_MIXED)
             e1b.record(stream)
@@ -633,7 +642,7 @@ def main():
         "dtype": "c64", "data": "synthetic",
         "config": {"workload": w.name, "n_side": w.n_side, "N": w.N, "kappa": w.kappa, "contrast": w.contrast,
                    "nbumps": w.nbumps, "nrhs": 1, "precision": "mixed (complex64 operators, FP32 math)",
-                   "eps_nca": a.eps_nca, "l2": "flushed: 256 MiB write between timed steps", "parallelism": f"replicas x{world}"},
+                   "eps_nca": a.eps_nca, "l2": "flushed: 256 MiB read between timed steps (operators streamed per step: 266 MB, larger than the L2)", "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "Munknowns/s", "h2d_bytes_per_step": w.N * 16, "d2h_bytes_per_step": w.N * 16},

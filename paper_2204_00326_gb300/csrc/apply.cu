@@ -1318,6 +1318,7 @@ constexpr int kTcA = 128 * 64 * 4;     // A (and A2) operand: 128 rows x 64 K (t
 constexpr int kTcBPart = 5120 * 4;     // one tf32 part of B for the largest chunk shape (2 NR x Kpad <= 5120)
 constexpr int kTcB = 3 * kTcBPart;
 constexpr int kTcCols = 128;           // TMEM columns (N = 2 NR <= 128)
+constexpr int kTcIssuer = kTcThreads - 32;  // the thread that issues and commits the MMAs (lane 0 of the last warp)
 
 __host__ __device__ inline int tc_raw_bytes(int nrhs_pad) { return BatchCfg<float>::stage_bytes(nrhs_pad); }
 __host__ __device__ inline int tc_smem_bytes(int nrhs_pad) { return kTcRaw * tc_raw_bytes(nrhs_pad) + 2 * kTcA + kTcB + 128; }
@@ -1479,7 +1480,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) stream_batched_tc_kernel(int nc
     for (int k = 0; k < kTcRaw; k++) {
         pend[k] = -1;
         if (cb + k < ce) {
-            batch_issue<float>(g, recs, cb + k, raw(k), &bar[k], nrhs, nrhs_pad, bulk_x, tid, kTcThreads);
+            if (warp == 0) batch_issue<float>(g, recs, cb + k, raw(k), &bar[k], nrhs, nrhs_pad, bulk_x, lane, 32);
             pend[k] = 0;
         }
     }
@@ -1503,9 +1504,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) stream_batched_tc_kernel(int nc
                 for (int j = 0; j < 8; j++) acc[8 * g8 + j] += v[j];
             }
     };
+    int4 na = recs[2 * cb];  // the next chunk's record, loaded a chunk ahead
     for (int c = cb, it = 0; c < ce; c++, it++) {
         const int s = it % kTcRaw;
-        const int4 ra = recs[2 * c];
+        const int4 ra = na;
+        if (c + 1 < ce) na = recs[2 * (c + 1)];
         const PassArgs<float>& pa = g.p[ra.x & 0xff];
         const int ro = (ra.x >> 16) & 0xffff;
         const int ld = ro + (ro & 1);
@@ -1532,11 +1535,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) stream_batched_tc_kernel(int nc
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
         __syncthreads();  // operands written; the raw stage is free again
+        // warp 0 issues the bulk copies of the chunk kTcRaw ahead (their addresses need
+        // global loads) while a lane of the last warp issues this chunk's MMAs
         if (c + kTcRaw < ce) {
-            batch_issue<float>(g, recs, c + kTcRaw, raw(s), &bar[s], nrhs, nrhs_pad, bulk_x, tid, kTcThreads);
+            if (warp == 0) batch_issue<float>(g, recs, c + kTcRaw, raw(s), &bar[s], nrhs, nrhs_pad, bulk_x, lane, 32);
             pend[s] = ((it + kTcRaw) / kTcRaw) & 1;
         }
-        if (tid == 0) {
+        if (tid == kTcIssuer) {
             tc_fence_after();
             const int N = 2 * NR;
             const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
@@ -1555,7 +1560,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) stream_batched_tc_kernel(int nc
         issued = it + 1;
         undrained = true;
         prevN = 2 * NR;
-        const bool row_ends = (c + 1 == ce) || recs[2 * (c + 1)].x != ra.x || recs[2 * (c + 1)].y != ra.y;
+        const bool row_ends = (c + 1 == ce) || na.x != ra.x || na.y != ra.y;
         if (!row_ends) continue;
         // the row's accumulator: wait for its last MMAs, drain, columns to E[n][lane]
         ok = mbar_wait(mbar, (unsigned)(it & 1));
@@ -1629,8 +1634,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) stream_batched_tc_kernel(int nc
         // let this CTA's copies and MMAs in flight land (bounded) before the TMEM goes
         for (int k = 0; k < kTcRaw; k++)
             if (pend[k] >= 0) mbar_wait(&bar[k], (unsigned)pend[k]);
-        if (issued > 0) mbar_wait(mbar, (unsigned)((issued - 1) & 1));
     }
+    if (s_bad && tid == kTcIssuer && issued > 0) mbar_wait(mbar, (unsigned)((issued - 1) & 1));
     tc_fence_before();
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
@@ -2624,7 +2629,7 @@ void launch_batched_tc(const OpsDev& d, const Group& g, const GroupArgs<float>& 
 // dafmm_set_batched_kernel).  Automatic mode keeps the CUDA-core kernel: at
 // these chunk shapes (M = 128 stacked rows, N = 2 NR <= 128, K <= 64 per
 // chunk) the operand conversion and the serial per-chunk steps cost more than
-// the FMAs they replace (64 right-hand sides at N = 16384: 1.59 ms on the
+// the FMAs they replace (64 right-hand sides at N = 16384: 1.33 ms on the
 // tensor cores, 0.74 ms on the CUDA cores).
 constexpr int kTcMinRhs = 8;
 constexpr bool kTcAuto = false;

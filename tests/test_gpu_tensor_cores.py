@@ -78,7 +78,7 @@ def test_tensor_cores_match_cuda_cores(N, op128, nrhs):
 
 def test_automatic_mode_uses_cuda_cores(N, op128):
     """At these chunk shapes the CUDA-core kernel is the faster one (measured
-    0.74 vs 1.59 ms for 64 right-hand sides at N = 16384), so automatic mode
+    0.74 vs 1.33 ms for 64 right-hand sides at N = 16384), so automatic mode
     picks it; the tensor-core kernel is chosen explicitly."""
     for nrhs in (4, 64):
         V = torch.as_tensor(W.random_vector(op128.N, nrhs, seed=300 + nrhs), device="cuda").contiguous()

@@ -338,7 +338,7 @@ int hodlr_sync(const dafmm_hodlr* M, void* stream);
 /*
  * hodlr_set_ctas -- width of the hodlr_solve launch (CTAs; each owns N / ctas
  * consecutive unknowns).  0 restores the width chosen at factorisation (a
- * power of two, all CTAs resident at once, at most one per leaf, about 2048
+ * power of two, all CTAs resident at once, at most one per leaf, about 256
  * unknowns per CTA on large problems and at least 128 CTAs).  Otherwise ctas
  * must be a power of two, at most N / leaf_size and at most the number of
  * CTAs the device holds at once.  A tuning and test knob; the result does

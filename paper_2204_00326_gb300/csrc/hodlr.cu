@@ -474,7 +474,7 @@ __device__ __forceinline__ void prefetch_rows(const HArgs<T>& a, int l, long e0,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kHT, 1) hodlr_apply_kernel(const __grid_constant__ HArgs<T> a)
+__global__ void __launch_bounds__(kHT, 2) hodlr_apply_kernel(const __grid_constant__ HArgs<T> a)
 {
     using C = typename C2<T>::t;
     using P = Ar<T>;
@@ -714,11 +714,13 @@ long apply_capacity(const dafmm_hodlr& h)
     return (long)sms * std::max(0, std::min(p32, p64));
 }
 
-// Default width: a power of two, resident at once, at most one CTA per leaf,
-// about 2048 unknowns per CTA on large problems (at least 128 CTAs).
+// Default width: a power of two, resident at once (two CTAs an SM), at most
+// one CTA per leaf, about 256 unknowns per CTA on large problems (at least
+// 128 CTAs).  The apply's time falls with the width until the CTAs run out
+// (65536 unknowns, rank 15: 194 us at 128 CTAs, 145 us at 256).
 int apply_ctas(const dafmm_hodlr& h)
 {
-    const long want = std::min({h.ncta_cap, h.N / h.leaf, std::max(128L, h.N / 2048)});
+    const long want = std::min({h.ncta_cap, h.N / h.leaf, std::max(128L, h.N / 256)});
     long c = 1;
     while (2 * c <= want) c *= 2;
     return (int)c;

@@ -157,12 +157,13 @@ def test_training_is_reproducible(N):
 
 def test_learned_guess_is_accepted_and_costs_no_iterations(N):
     """Trained on 256 solver solutions (64 x 64, kappa = 20), the guess of a
-    held-out problem is accepted with |f - A x0| / |f| < 0.9 (a zero guess
-    has 1; training is not bit-reproducible, since the weight gradients are
-    summed with FP32 atomics, and runs gave 0.28 to 0.55); HODLR-
-    preconditioned GMRES from it needs no more iterations than from zero; the
-    nonlinear coarse correction inside flexible GMRES converges.  (How many
-    iterations the guess saves is measured, not asserted: bench.py --learned.)"""
+    held-out problem is accepted with |f - A x0| / |f| < 0.75 (a zero guess
+    has 1; training is reproducible bit for bit, and this network reaches
+    0.59); HODLR-preconditioned GMRES from it needs no more iterations than
+    from zero; the nonlinear coarse correction inside flexible GMRES
+    converges.  (The larger network of bench.py --learned saves one of 11
+    iterations at this size and costs more time in inference than it saves:
+    the gain is measured there, not asserted.)"""
     from paper_2204_00326_gb300 import learned as Lr
     from paper_2204_00326_gb300.operator import DafmmOperator
 
@@ -182,7 +183,7 @@ def test_learned_guess_is_accepted_and_costs_no_iterations(N):
                 z, g = res["zero_guess"], res["learned_guess"]
                 print("learned guess:", g["guess_residual"], "iterations", g["iterations"], "vs", z["iterations"])
                 assert z["converged"] and g["converged"] and g["rel_residual"] <= 1e-8
-                assert g["guess_used"] and 0 < g["guess_residual"] < 0.9, res
+                assert g["guess_used"] and 0 < g["guess_residual"] < 0.75, res
                 assert g["iterations"] <= z["iterations"], res
                 fd = torch.as_tensor(f, device="cuda")
                 x = torch.zeros_like(fd)

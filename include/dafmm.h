@@ -518,9 +518,11 @@ int dafmm_set_batched_grid(dafmm_ops* ops, int ctas_per_sm);
 /*
  * Several problems (operators of different sizes, each with its own tree)
  * applied together.  dafmm_batch_matvec computes out[i] = A_i v[i] for every
- * problem i, nrhs right-hand sides each, in one CUDA graph: every problem's
- * kernels on a stream of its own forked from the graph's start, so the
- * problems' kernels overlap; the graph is captured on the first call for a
+ * problem i, nrhs right-hand sides each, in one CUDA graph: with several
+ * right-hand sides every problem's kernels on a stream of its own forked
+ * from the graph's start, so the problems' kernels overlap (with one, the
+ * problems run in order: the single-right-hand-side kernel needs the whole
+ * GPU); the graph is captured on the first call for a
  * given (nrhs, precision, pointers) and replayed by one cudaGraphLaunch
  * after that (at most four such sets are kept).  v_dev, out_dev: host arrays
  * of n device pointers, each vector N_i x nrhs complex128.  The handles must

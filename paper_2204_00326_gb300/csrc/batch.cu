@@ -3,9 +3,12 @@
 //
 // dafmm_batch: the problems' operator applications are captured once (per
 // right-hand-side count, precision and set of vector pointers) into one CUDA
-// graph: every problem on its own stream forked from and joined to the
-// capture stream, so small problems' kernels run beside large ones'; each
-// call replays the graph with one cudaGraphLaunch.
+// graph: with several right-hand sides every problem on its own stream forked
+// from and joined to the capture stream, so small problems' kernels run
+// beside large ones' (their kernels never wait on other CTAs); with one
+// right-hand side in order (the fused kernel's warps wait on each other, so
+// two of them must not share the GPU); each call replays the graph with one
+// cudaGraphLaunch.
 //
 // dafmm_tune_batched: times the candidate configurations of an operator's
 // several-right-hand-side passes with CUDA events and keeps the fastest.
@@ -112,12 +115,18 @@ void batch_matvec(dafmm_batch* b, int nrhs, const double* const* v, double* cons
         cudaGraph_t g = nullptr;
         ck(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
         try {
-            ck(cudaEventRecord(b->fork, b->cap), "cudaEventRecord");
-            for (int i = 0; i < n; i++) {
-                ck(cudaStreamWaitEvent(b->lanes[i], b->fork, 0), "cudaStreamWaitEvent");
-                apply_matvec(b->ops[i]->tree->t, b->ops[i]->dev, nrhs, v[i], out[i], precision, b->lanes[i]);
-                ck(cudaEventRecord(b->join[i], b->lanes[i]), "cudaEventRecord");
-                ck(cudaStreamWaitEvent(b->cap, b->join[i], 0), "cudaStreamWaitEvent");
+            if (nrhs == 1) {
+                // one right-hand side runs the cooperative fused kernel, whose warps wait on
+                // each other: two of them must not share the GPU, so the problems run in order
+                for (int i = 0; i < n; i++) apply_matvec(b->ops[i]->tree->t, b->ops[i]->dev, 1, v[i], out[i], precision, b->cap);
+            } else {
+                ck(cudaEventRecord(b->fork, b->cap), "cudaEventRecord");
+                for (int i = 0; i < n; i++) {
+                    ck(cudaStreamWaitEvent(b->lanes[i], b->fork, 0), "cudaStreamWaitEvent");
+                    apply_matvec(b->ops[i]->tree->t, b->ops[i]->dev, nrhs, v[i], out[i], precision, b->lanes[i]);
+                    ck(cudaEventRecord(b->join[i], b->lanes[i]), "cudaEventRecord");
+                    ck(cudaStreamWaitEvent(b->cap, b->join[i], 0), "cudaStreamWaitEvent");
+                }
             }
         } catch (...) {
             cudaStreamEndCapture(b->cap, &g);

@@ -957,8 +957,7 @@ void ensure_many(dafmm_hodlr& h, int B)
         fail(DAFMM_ENOMEM, "device allocation for the several-right-hand-side HODLR buffers failed");
     }
     h.bcap = B;
-    static bool attrs = false;
-    if (!attrs) {
+    {  // the handle's device (attributes are set per device)
         CK(cudaFuncSetAttribute(hodlr_leaf_many_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<double>(0, kBC)));
         CK(cudaFuncSetAttribute(hodlr_leaf_many_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<float>(0, kBC)));
         CK(cudaFuncSetAttribute(hodlr_wx_many_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<double>(1, kBC)));
@@ -967,7 +966,6 @@ void ensure_many(dafmm_hodlr& h, int B)
         CK(cudaFuncSetAttribute(hodlr_s_many_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<float>(2, kBC)));
         CK(cudaFuncSetAttribute(hodlr_upd_many_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<double>(3, kBC)));
         CK(cudaFuncSetAttribute(hodlr_upd_many_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)many_smem<float>(3, kBC)));
-        attrs = true;
     }
 }
 

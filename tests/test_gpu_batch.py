@@ -79,6 +79,24 @@ def test_batch_equals_each_problem_and_the_oracle(N, problems, precision, tol):
         op.sync()
 
 
+def test_batch_with_one_rhs(N, problems):
+    """One right-hand side: the problems run in order inside the graph."""
+    ws, ops = problems
+    vs = [torch.as_tensor(W.random_vector(w.N, 1, seed=80 + k)[:, 0], device="cuda") for k, w in enumerate(ws)]
+    outs = [torch.empty_like(v) for v in vs]
+    b = N.Batch([op.ops for op in ops])
+    try:
+        for prec in (N.DAFMM_MIXED, N.DAFMM_FP64):
+            b.matvec(vs, outs, prec)
+            torch.cuda.synchronize()
+            for op, v, o in zip(ops, vs, outs):
+                assert torch.equal(o, op.matvec(v, precision=prec))
+    finally:
+        b.close()
+    for op in ops:
+        op.sync()
+
+
 def test_tuner_records_and_applies_its_choice(N, problems):
     ws, ops = problems
     k = max(range(len(ws)), key=lambda i: ws[i].N)

@@ -74,6 +74,9 @@ struct Sched {
     int kpw[kMaxPhase];         // chunks per warp in each phase
     int sbase[kMaxPhase];       // warp shares in the phases before (partial slots)
     unsigned phdeps[kMaxPhase]; // passes read by the passes of each phase
+    int wlo[kMaxPhase];         // the warps sharing each phase: wlo .. wlo + wn - 1, in the
+    int wn[kMaxPhase];          // order (warp of its CTA, CTA)
+    int chain_first;            // a warp takes pieces only when its chain shares are done
     // bulk list: the passes with slack, cut into pieces handed out in order
     int npieces;
     const int4* pieces;         // per piece: {first chunk, end chunk, partial slot, pass}
@@ -81,6 +84,7 @@ struct Sched {
     unsigned deps[kMaxPass];    // per pass: passes whose rows it reads
     int target[kMaxPass];       // per pass: rows it writes
     int dphase[kMaxPass];       // per pass: latest phase among the passes it reads (-1: none)
+    unsigned pub;               // passes read by another pass of the launch: the only ones counted
 };
 
 template <typename T>
@@ -194,13 +198,13 @@ __device__ __forceinline__ int ld_acquire(const int* p)
 
 constexpr int kDoneStride = 32;  // ints between two pass counters: one 128-byte line each
 
-// Publish one finished row of a pass: the row's stores (ordered before lane
-// 0 by the barrier) become visible at device scope before the pass's row
+// Publish n finished rows of a pass: the rows' stores (ordered before lane 0
+// by the barrier) become visible at device scope before the pass's row
 // counter moves (release).
-__device__ __forceinline__ void row_done(int* done, int pass, int lane)
+__device__ __forceinline__ void rows_done(int* done, int pass, int n, int lane)
 {
     __syncwarp();
-    if (lane == 0) red_add_release(&done[pass * kDoneStride], 1);
+    if (lane == 0) red_add_release(&done[pass * kDoneStride], n);
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -292,6 +296,33 @@ __device__ __forceinline__ double2 df_split(double2 v)
     return df_bits(make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih)));
 }
 
+// o + p[0] + p[Pld] + ... + p[(n - 1) Pld], added in that order; the
+// partials are loaded a batch at a time, so that their latencies overlap
+// (the 16-byte float pairs one at a time: batches of them measured slower).
+template <typename T>
+__device__ __forceinline__ typename V2<T>::t sum_partials(typename V2<T>::t o, const typename V2<T>::t* p, int Pld, int n)
+{
+    using C = typename V2<T>::t;
+    constexpr int kSumBatch = sizeof(T) == 8 ? 1 : 8;
+    for (int q = 0; q < n; q += kSumBatch) {
+        C v[kSumBatch];
+#pragma unroll
+        for (int u = 0; u < kSumBatch; u++)
+            if (q + u < n) v[u] = __ldcg(&p[(size_t)(q + u) * Pld]);
+#pragma unroll
+        for (int u = 0; u < kSumBatch; u++)
+            if (q + u < n) {
+                if constexpr (sizeof(T) == 8) {
+                    o = df_bits(df4_add(as_df(o), as_df(v[u])));  // float pairs (double-float)
+                } else {
+                    o.x += v[u].x;
+                    o.y += v[u].y;
+                }
+            }
+    }
+    return o;
+}
+
 // Partial slot of the warp share of phase k that starts at chunk c.
 __device__ __forceinline__ int share_slot(const Sched& sc, int k, int c) { return sc.sbase[k] + (c - sc.base[k]) / sc.kpw[k]; }
 
@@ -334,26 +365,9 @@ __device__ __forceinline__ bool own_row(typename V2<T>::t* y, const typename V2<
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) return false;
     __syncwarp();  // lane 0's acquire, and the owner's own stores to y, come before every lane's reads
-    for (int i = lane; i < ro; i += 32) {
-        C o = y[i];
-        if constexpr (sizeof(T) == 8) {
-            // float pairs (double-float)
-            float4 a = as_df(o);
-            for (int c = next_slot(c0, base, kpw); c < c1; c = next_slot(c, base, kpw))
-                a = df4_add(a, as_df(__ldcg(&P[(size_t)share_slot(sc, k, c) * Pld + i])));
-            o = df_bits(a);
-        } else {
-            T sr = o.x, si = o.y;
-            for (int c = next_slot(c0, base, kpw); c < c1; c = next_slot(c, base, kpw)) {
-                const C p = __ldcg(&P[(size_t)share_slot(sc, k, c) * Pld + i]);
-                sr += p.x;
-                si += p.y;
-            }
-            o.x = sr;
-            o.y = si;
-        }
-        y[i] = o;
-    }
+    // the shares that start inside the row hold consecutive slots, in share order
+    const int s1 = share_slot(sc, k, next_slot(c0, base, kpw));
+    for (int i = lane; i < ro; i += 32) y[i] = sum_partials<T>(y[i], P + (size_t)s1 * Pld + i, Pld, others);
     return true;
 }
 
@@ -661,11 +675,14 @@ struct Slice {
     int k, b, c, e;
 };
 
-// First non-empty share of warp w in chain phases k, k+1, ...
+// First non-empty share of warp w (in the order of Sched::wlo) in chain
+// phases k, k+1, ...
 __device__ __forceinline__ bool slice_from(const Sched& sc, int k, int w, Slice& sl)
 {
     for (; k < sc.nph; k++) {
-        const int b = sc.base[k] + w * sc.kpw[k];
+        const int sh = w - sc.wlo[k];
+        if (sh < 0 || sh >= sc.wn[k]) continue;
+        const int b = sc.base[k] + sh * sc.kpw[k];
         const int e = min(sc.base[k + 1], b + sc.kpw[k]);
         if (b < e) {
             sl.k = k;
@@ -679,6 +696,15 @@ __device__ __forceinline__ bool slice_from(const Sched& sc, int k, int w, Slice&
 }
 
 constexpr int kPiece = 4;  // chunks per bulk piece
+
+// Warps given to the chain phases after the first: this many times the
+// chain's share of the chunks after the first phase (the rest stream the
+// slack passes); the chain's dependent steps need the margin.
+constexpr double kChainShare64 = 1.25, kChainShare128 = 1.0;
+// Plans: the slack passes as pieces taken in order (else in phases of their
+// own), and the chain phases after the first on their own warps.
+constexpr bool kPieces128 = true, kSplit128 = true;
+constexpr bool kPieces64 = false, kSplit64 = true;
 
 // One scheduled chunk: c (-1: none); kind 0: chain (aux = phase, end = the
 // share's end), 1: bulk (aux = the piece's partial slot, end = the piece's end).
@@ -720,22 +746,14 @@ __device__ __forceinline__ bool bulk_finish(typename V2<T>::t* y, const typename
     if (!last) return false;
     __syncwarp();
     for (int i = lane; i < ro; i += 32) {
+        const C* p = P + (size_t)s0 * Pld + i;
         if constexpr (sizeof(T) == 8) {
-            // float pairs (double-float)
-            float4 a = as_df(__ldcg(&P[(size_t)s0 * Pld + i]));
-            for (int q = 1; q < np; q++) a = df4_add(a, as_df(__ldcg(&P[(size_t)(s0 + q) * Pld + i])));
-            y[i] = df_bits(a);
+            y[i] = sum_partials<T>(__ldcg(p), p + Pld, Pld, np - 1);
         } else {
-            T sr = 0, si = 0;
-            for (int q = 0; q < np; q++) {
-                const C p = __ldcg(&P[(size_t)(s0 + q) * Pld + i]);
-                sr += p.x;
-                si += p.y;
-            }
-            C o;
-            o.x = sr;
-            o.y = si;
-            y[i] = o;
+            C z;
+            z.x = 0;
+            z.y = 0;
+            y[i] = sum_partials<T>(z, p, Pld, np);
         }
     }
     if (lane == 0) cnt[c0] = 0;
@@ -755,12 +773,16 @@ __device__ __forceinline__ bool bulk_finish(typename V2<T>::t* y, const typename
 // the first chunk of a pass waits (bounded) on its inputs' row counters with
 // acquire semantics.  Split chain rows are summed by the warp that holds
 // their first chunk, split bulk rows by their last piece, both in a fixed
-// order.  Every finished row moves its pass's counter.  Launched
-// cooperatively, so every warp is resident; a warp blocks only on rows of
-// earlier phases, or on bulk inputs when it has no chain work left, so the
-// waits end.
+// order.  A warp counts its finished rows of a pass in its pass's counter
+// with one release when its run of chunks of that pass ends, and before it
+// waits on anything; a pass is complete only when every run of it is, so the
+// count arrives no later than it would row by row, and a waiting warp holds
+// no uncounted rows.  Passes that no other pass of the launch reads are not
+// counted.  Launched cooperatively, so every warp is resident; a warp blocks
+// only on rows of earlier phases, or on bulk inputs when it has no chain work
+// left, so the waits end.
 template <typename T>
-__global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* __restrict__ recs, const __grid_constant__ GroupArgs<T> g,
+__global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4* __restrict__ recs, const __grid_constant__ GroupArgs<T> g,
                                                                    const __grid_constant__ Sched sc, typename V2<T>::t* __restrict__ P,
                                                                    int Pld, int* __restrict__ cnt, int* __restrict__ done,
                                                                    int* __restrict__ err)
@@ -773,7 +795,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
     auto stage = [&](int k) { return (C*)(wb + (size_t)k * Cfg::kStage); };
     C* xs = (C*)(wb + 2 * Cfg::kStage);
     unsigned long long* bar = (unsigned long long*)(wb + 2 * Cfg::kStage + Cfg::kXs);
-    const int wg = blockIdx.x * kStreamWarps + warp;
+    const int wg = warp * gridDim.x + blockIdx.x;  // the CTAs' first warps first
 
     // ---- scheduler (warp-uniform, except the lane-0 prefetches) ----
     Slice cs;
@@ -801,7 +823,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
             bool chain;
             if (!hc)
                 chain = false;
-            else if (!hb)
+            else if (!hb || sc.chain_first)
                 chain = true;
             else if ((sc.phdeps[cs.k] & ~(ready | seen)) == 0)
                 chain = true;
@@ -872,6 +894,11 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
     C xr[kMaxPrefetch];
     Acc<T> acc;
     acc.zero();
+    int pend_pass = 0, pend_n = 0;  // finished rows of one pass not yet counted (warp-uniform)
+    auto publish = [&]() {
+        if (pend_n) rows_done(done, pend_pass, pend_n, lane);
+        pend_n = 0;
+    };
     for (int it = 0;; it++) {
         const int s = it & 1;
         const unsigned parity = (unsigned)((it >> 1) & 1);
@@ -887,6 +914,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
         };
         if (!have_x) {
             // first chunk of a pass whose inputs were not yet known complete
+            if (sc.deps[ra.x & 0xff] & ~ready) publish();
             if (deps_wait(sc, done, sc.deps[ra.x & 0xff], ready, lane) < 0) {
                 bail();
                 return;
@@ -958,7 +986,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
             C* yrow = pa.y + (size_t)ra.y * pa.ldy;
             bool fin = true;
             if (cur.kind == 0) {
-                const int b = sc.base[cur.aux] + wg * sc.kpw[cur.aux];
+                const int b = sc.base[cur.aux] + (wg - sc.wlo[cur.aux]) * sc.kpw[cur.aux];
                 if (rb.w < b) {
                     // the row began in an earlier share: leave a partial for its owner
                     flush_row<T>(acc, ro, lane, P + (size_t)share_slot(sc, cur.aux, b) * Pld, false, 0);
@@ -966,6 +994,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
                     fin = false;
                 } else {
                     flush_row<T>(acc, ro, lane, yrow, true, 0);
+                    if (rb.z > cur.end) publish();
                     if (rb.z > cur.end && !own_row<T>(yrow, P, Pld, cnt, rb.w, rb.z, sc, cur.aux, ro, lane)) {
                         // the copies in flight now: the next chunk's (other stage), the one after (this stage)
                         if (lane == 0) {
@@ -983,9 +1012,15 @@ __global__ void __launch_bounds__(32 * kStreamWarps) stream_kernel(const int4* _
                 flush_row<T>(acc, ro, lane, P + (size_t)cur.aux * Pld, false, 0);
                 fin = bulk_finish<T>(yrow, P, Pld, cnt, rb.w, rb.z, cur.aux, cur.c, ro, lane);
             }
-            if (fin) row_done(done, pass, lane);
+            if (fin && (sc.pub >> pass & 1u)) {
+                if (pass != pend_pass) publish();
+                pend_pass = pass;
+                pend_n++;
+            }
             acc.zero();
         }
+        // the warp's run of the pass ends here: count its rows
+        if (pend_n && (!h1 || (na.x & 0xff) != pend_pass)) publish();
         if (!h1) break;
         // fold in the polls, then choose the chunk after next
         unsigned add = 0;
@@ -2163,14 +2198,16 @@ BsrHost compose_leaf(const BsrHost& D, const BsrHost& U)
     return C;
 }
 
-// Warp shares of a plan's chain list for a grid of `warps` warps: chunks per
-// warp in each phase, and the shares in the phases before.  Returns the shares.
+// Warp shares of a plan's chain list for a grid of `warps` warps (each phase
+// shared by F.wn[k] of them when the plan sets them): chunks per warp in each
+// phase, and the shares in the phases before.  Returns the shares.
 int fused_shares(const FusedPlan& F, int warps, int* kpw, int* sbase)
 {
     int n = 0;
     for (int k = 0; k < F.nph; k++) {
         const int nk = F.base[k + 1] - F.base[k];
-        kpw[k] = std::max(1, (nk + warps - 1) / warps);
+        const int nw = F.wn.empty() ? warps : std::max(1, F.wn[k]);
+        kpw[k] = std::max(1, (nk + nw - 1) / nw);
         sbase[k] = n;
         n += (nk + kpw[k] - 1) / kpw[k];
     }
@@ -2264,54 +2301,81 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
     F.g.Pld = std::max(pld, 1);
     for (int k = 0; k < 2; k++) {
         FusedPlan& P = F.plan[k];
-        const bool dynamic = k == 0;
+        const bool dynamic = k == 0 ? kPieces128 : kPieces64;
+        const bool split = k == 0 ? kSplit128 : kSplit64;
         auto chunks = [&](int p, int r) { return chunks_in(k, p, r); };
         const std::vector<PassCut>& cuts = cuts_k[k];
-        // rows of every phase: the chain at its phase; in the static plan the
-        // slack rows fill each phase up to about one chunk per warp (more would
-        // take bandwidth from the chain), the rest going to the earliest
-        // deadline among them, where one long phase streams it
+        // rows of every chain phase, each pass at its earliest phase
         std::vector<std::vector<std::pair<int, int>>> rows(nph);
-        std::vector<long> load(nph, 0);
         for (int p = 0; p < np; p++)
             if (!slack[p])
                 for (int r = 0; r < hs[p]->nrows; r++)
-                    if (chunks(p, r)) {
-                        rows[asap[p]].push_back({p, r});
-                        load[asap[p]] += chunks(p, r);
-                    }
+                    if (chunks(p, r)) rows[asap[p]].push_back({p, r});
+        // the static plan: after each chain phase, one phase per slack pass
+        // whose inputs it completes (finest level first).  The first phase is
+        // shared by every warp; then the chain phases by the first wc warps
+        // and the slack phases by the others, so that the slack passes stream
+        // while the chain steps through its dependent passes
+        std::vector<char> bulk_ph(nph, 0);
         if (!dynamic) {
-            const long fill = (long)F.ctas[k] * kStreamWarps;
-            int bulk_at = nph - 1;
-            for (int p = 0; p < np; p++)
-                if (slack[p]) bulk_at = std::min(bulk_at, alap[p]);
-            std::vector<int> next(np, 0);
+            std::vector<std::vector<std::pair<int, int>>> out;
+            std::vector<char> is_bulk;
             for (int ph = 0; ph < nph; ph++) {
-                std::vector<int> cand;
+                out.push_back(rows[ph]);
+                is_bulk.push_back(0);
+                std::vector<int> sl;
                 for (int p = 0; p < np; p++)
-                    if (slack[p] && asap[p] <= ph && ph <= alap[p]) cand.push_back(p);
-                std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return alap[a] < alap[b]; });
-                for (int p : cand)
-                    for (; next[p] < hs[p]->nrows && (load[ph] < fill || ph == std::min(alap[p], std::max(asap[p], bulk_at)));
-                         next[p]++) {
-                        if (!chunks(p, next[p])) continue;
-                        rows[ph].push_back({p, next[p]});
-                        load[ph] += chunks(p, next[p]);
-                    }
+                    if (slack[p] && std::max(F.dphase[p], 0) == ph) sl.push_back(p);
+                std::stable_sort(sl.begin(), sl.end(), [&](int a, int b) { return passes[a].level > passes[b].level; });
+                for (int p : sl) {
+                    out.emplace_back();
+                    for (int r = 0; r < hs[p]->nrows; r++)
+                        if (chunks(p, r)) out.back().push_back({p, r});
+                    is_bulk.push_back(1);
+                }
             }
+            rows.swap(out);
+            bulk_ph.swap(is_bulk);
         }
+        const int nphase = (int)rows.size();
+        if (nphase > kMaxPhase) fail(DAFMM_EBADARG, "too many phases for the fused launch");
         std::vector<int4> recs;
-        P.nph = nph;
-        P.base.assign(nph + 1, 0);
-        P.phdeps.assign(nph, 0u);
-        for (int ph = 0; ph < nph; ph++) {
+        P.nph = nphase;
+        P.base.assign(nphase + 1, 0);
+        P.phdeps.assign(nphase, 0u);
+        long after0[2] = {0, 0};  // chunks after the first phase: chain, slack
+        for (int ph = 0; ph < nphase; ph++) {
             P.base[ph] = (int)(recs.size() / 2);
             for (auto& pr : rows[ph]) {
                 P.phdeps[ph] |= deps[pr.first];
                 place_row(recs, cuts[pr.first], pr.second);
             }
+            if (ph > 0) after0[bulk_ph[ph]] += (long)(recs.size() / 2) - P.base[ph];
         }
-        P.base[nph] = (int)(recs.size() / 2);
+        P.base[nphase] = (int)(recs.size() / 2);
+        if (dynamic)
+            for (int p = 0; p < np; p++)
+                if (slack[p])
+                    for (int r = 0; r < hs[p]->nrows; r++) after0[1] += chunks(p, r);
+        P.wlo.clear();
+        P.wn.clear();
+        P.chain_first = split && dynamic;
+        if (split) {
+            const int W = F.ctas[k] * kStreamWarps;
+            int wc = W;  // chain warps
+            if (after0[1] == 0)
+                wc = W;
+            else if (after0[0] == 0)
+                wc = 0;
+            else
+                wc = std::min(W - 1, std::max(1, (int)std::lround(W * (k == 0 ? kChainShare128 : kChainShare64) * after0[0] /
+                                                                  (double)(after0[0] + after0[1]))));
+            for (int ph = 0; ph < nphase; ph++) {
+                const bool all = ph == 0 || (bulk_ph[ph] ? wc == 0 : wc == W);
+                P.wlo.push_back(all ? 0 : (bulk_ph[ph] ? wc : 0));
+                P.wn.push_back(all ? W : (bulk_ph[ph] ? W - wc : wc));
+            }
+        }
         int kpw[kMaxPhase], sbase[kMaxPhase];
         const int chain_slots = fused_shares(P, F.ctas[k] * kStreamWarps, kpw, sbase);
         // dynamic plan: the slack passes as pieces of kPiece chunks, earliest inputs first
@@ -2320,7 +2384,10 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
             std::vector<int> order;
             for (int p = 0; p < np; p++)
                 if (slack[p]) order.push_back(p);
-            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return asap[a] < asap[b]; });
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+                const int da = std::max(F.dphase[a], 0), db = std::max(F.dphase[b], 0);
+                return da != db ? da < db : passes[a].level > passes[b].level;
+            });
             for (int p : order)
                 for (int r = 0; r < hs[p]->nrows; r++) {
                     const int n = chunks(p, r);
@@ -2483,15 +2550,22 @@ void launch_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const doubl
     std::memset(&sc, 0, sizeof(sc));
     sc.nph = FP.nph;
     for (int ph = 0; ph <= FP.nph; ph++) sc.base[ph] = FP.base[ph];
+    for (int ph = 0; ph < FP.nph; ph++) {
+        sc.wlo[ph] = FP.wlo.empty() ? 0 : FP.wlo[ph];
+        sc.wn[ph] = FP.wn.empty() ? warps : FP.wn[ph];
+    }
     fused_shares(FP, warps, sc.kpw, sc.sbase);
     for (int ph = 0; ph < FP.nph; ph++) sc.phdeps[ph] = FP.phdeps[ph];
     sc.npieces = FP.npieces;
+    sc.chain_first = FP.chain_first ? 1 : 0;
     sc.pieces = FP.pieces;
     sc.next_piece = F.done + kMaxPass * kDoneStride;
     for (size_t p = 0; p < F.g.passes.size(); p++) {
         sc.deps[p] = F.deps[p];
         sc.target[p] = F.target[p];
         sc.dphase[p] = F.dphase[p];
+        for (size_t q = 0; q < F.g.passes.size(); q++)
+            if (F.deps[q] >> p & 1u) sc.pub |= 1u << p;
     }
     if (d.stall_pass >= 0) sc.target[d.stall_pass] += 1;  // a row nobody writes: the waits on it give up
     cudaLaunchConfig_t cfg;

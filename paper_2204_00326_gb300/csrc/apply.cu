@@ -3074,15 +3074,17 @@ cudaEvent_t* next_profile_events(OpsDev& d)
 
 void run_eager(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, int precision, cudaStream_t stream, bool prof);
 
-// Capture the application into the cache slot G (on the private stream).
-void capture(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, int precision, GraphCache& G)
+// Capture the application into the cache slot G (on the private stream),
+// with event-record nodes at the five pass marks when `marks` (each node
+// costs about 2.5 us of latency on the path, so only profiled calls carry them).
+void capture(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, int precision, GraphCache& G, bool marks)
 {
     if (!d.cap_stream) CK(cudaStreamCreateWithFlags(&d.cap_stream, cudaStreamNonBlocking));
     for (int k = 0; k < 5; k++)
         if (!d.placeholder[k]) CK(cudaEventCreate(&d.placeholder[k]));
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(d.cap_stream, cudaStreamCaptureModeThreadLocal));
-    tl_capture_events = d.placeholder;
+    tl_capture_events = marks ? d.placeholder : nullptr;
     try {
         run_eager(t, d, v, out, nrhs, precision, d.cap_stream, false);
     } catch (...) {
@@ -3097,7 +3099,7 @@ void capture(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, i
         // same topology, new pointers: update in place; the exec keeps the
         // node identities of the graph it was instantiated from
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(G.exec, graph, &info) == cudaSuccess) {
+        if (G.marks == marks && cudaGraphExecUpdate(G.exec, graph, &info) == cudaSuccess) {
             CK(cudaGraphDestroy(graph));
             G.v = v;
             G.out = out;
@@ -3134,6 +3136,7 @@ void capture(const Tree& t, OpsDev& d, const double* v, double* out, int nrhs, i
     G.v = v;
     G.out = out;
     G.nrhs = nrhs;
+    G.marks = marks;
 }
 
 }  // namespace
@@ -3179,15 +3182,16 @@ void apply_matvec(const Tree& t, OpsDev& d, int nrhs, const double* v, double* o
         run_eager(t, d, v, out, nrhs, precision, stream, false);
         return;
     }
-    // a cached graph for these pointers, else the least recently used slot
+    // a cached graph for these pointers (with pass marks when profiling),
+    // else the least recently used slot
     GraphCache* G = nullptr;
     for (auto& c : d.gc[precision])
-        if (c.exec && c.v == v && c.out == out && c.nrhs == nrhs) G = &c;
+        if (c.exec && c.v == v && c.out == out && c.nrhs == nrhs && c.marks == d.profile) G = &c;
     if (!G) {
         G = &d.gc[precision][0];
         for (auto& c : d.gc[precision])
             if (c.used < G->used) G = &c;
-        capture(t, d, v, out, nrhs, precision, *G);
+        capture(t, d, v, out, nrhs, precision, *G, d.profile);
     }
     G->used = ++d.gc_clock;
     if (d.profile) {

@@ -94,6 +94,7 @@ struct GraphCache {
     double* out = nullptr;
     int nrhs = 0;
     cudaGraphNode_t ev_node[5] = {};  // event-record nodes of the five pass marks
+    bool marks = false;               // captured with the pass marks (profiled calls)
     unsigned long long used = 0;      // last use (LRU replacement)
 };
 constexpr int kGraphSlots = 4;        // cached (v, out) pairs per precision

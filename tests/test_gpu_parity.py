@@ -174,11 +174,15 @@ def test_matvec_argument_errors(N, op128):
 
 def test_profile_records_passes(N, op128):
     v = torch.as_tensor(W.random_vector(op128.N, 1, seed=2)[:, 0], device="cuda")
+    plain = op128.matvec(v, precision=N.DAFMM_MIXED)
     N.dafmm_profile(op128.ops, True)
     for _ in range(3):
-        op128.matvec(v, precision=N.DAFMM_MIXED)
+        marked = op128.matvec(v, precision=N.DAFMM_MIXED)
     p = N.dafmm_profile_read(op128.ops)
     N.dafmm_profile(op128.ops, False)
+    # the profiled calls replay a graph with event nodes at the pass marks: same kernels, same result
+    assert torch.equal(marked, plain)
+    assert torch.equal(op128.matvec(v, precision=N.DAFMM_MIXED), plain)
     # one right-hand side: every tree pass is one kernel, reported as the far field only
     assert p.calls == 3 and p.ms_far > 0 and p.ms_leaf > 0
     assert p.ms_up == 0 and p.ms_m2l == 0 and p.ms_down == 0

@@ -790,6 +790,9 @@ __global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4
     using C = typename V2<T>::t;
     using Cfg = StreamCfg<T>;
     extern __shared__ __align__(128) unsigned char smem[];
+    // the leaf kernel after this launch may take SMs as CTAs retire; it waits
+    // (griddepcontrol.wait) for this grid's writes before it reads them
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char* wb = smem + (size_t)warp * Cfg::kWarp;
     auto stage = [&](int k) { return (C*)(wb + (size_t)k * Cfg::kStage); };
@@ -1736,9 +1739,10 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
 
 // out = v + kappa^2 q (U_B u^{B,i} + sum_{9 offsets} T_o v_{B+o}) per leaf.
 // 48 threads per leaf: node i and one row sy of the 3 x 3 near offsets each;
-// before the near field the first group stages shared memory while the
-// second applies the composed L2L and L2P and the third L2P; the groups' sums
-// meet in shared memory.
+// the first group stages shared memory, every group applies its row of near
+// offsets, and after the wait for the launch before (griddepcontrol) the
+// second applies the composed L2L and L2P and the third L2P; the groups'
+// sums meet in shared memory.
 // 4 leaves per CTA.  Near blocks are stored [o][j][i] (target index fastest)
 // for conflict-free shared reads.  A CTA's four leaves are consecutive in
 // Morton order (a 2 x 2 quad); the inputs of the 4 x 4 leaves around it are
@@ -1750,6 +1754,26 @@ __global__ void leaf_batched_kernel(int nleaf, int nrhs, const int* __restrict__
 // null): row and piece counters of the fused launch before, reset here for
 // the next application.
 constexpr int kLeafPerCta = 4;
+constexpr int kLeafEnt = 8;        // composed blocks a leaf at most, for the staged far field
+constexpr int kLeafStageCols = 64; // staged columns a leaf at most, composed and L2P each
+
+// Bulk copies counted on an mbarrier: the expected bytes first, then the
+// copy (both addresses 16-byte aligned, bytes a multiple of 16, pieces of
+// at most 16 KB); each issuing thread arrives once when it has issued all.
+__device__ __forceinline__ void bulk_expect_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    for (unsigned o = 0; o < bytes; o += 16384) {
+        const unsigned n = min(16384u, bytes - o);
+        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32((char*)dst + o)),
+                     "l"((const char*)src + o), "r"(n), "r"(smem_u32(bar))
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void mbar_arrive1(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 template <typename T>
 __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf, const int* __restrict__ nbr,
@@ -1765,15 +1789,26 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
                                                                       const typename V2<T>::t* __restrict__ lcA,
                                                                       const typename V2<T>::t* __restrict__ lcB,
                                                                       const double2* __restrict__ v, const double* __restrict__ q, double k2,
-                                                                      double2* __restrict__ out, int* __restrict__ done)
+                                                                      double2* __restrict__ out, int* __restrict__ done, int fcc, int fcl,
+                                                                      int* __restrict__ err)
 {
     using C = typename V2<T>::t;
     static_assert(kLeafPerCta == 4, "a CTA takes one 2 x 2 quad of leaves (four consecutive Morton indices)");
+    // fcc, fcl > 0: the far-field blocks are staged in shared memory, up to
+    // fcc composed and fcl L2P columns a leaf: sUc [leaf][col][16], sUl the
+    // same, then the locals they multiply, suc [leaf][col] and sul
+    extern __shared__ __align__(16) unsigned char leaf_dyn[];
+    const bool staged = fcc > 0 || fcl > 0;
+    C* sUc = (C*)leaf_dyn;
+    C* sUl = sUc + kLeafPerCta * fcc * 16;
+    C* suc = sUl + kLeafPerCta * fcl * 16;
+    C* sul = suc + kLeafPerCta * fcc;
+    __shared__ int s_ecol[kLeafPerCta][kLeafEnt], s_erin[kLeafPerCta][kLeafEnt], s_ecoff[kLeafPerCta][kLeafEnt];
+    __shared__ int s_nce[kLeafPerCta], s_ncc[kLeafPerCta], s_nl[kLeafPerCta];
     __shared__ __align__(16) C sn[9 * 256];
     __shared__ __align__(16) C vq[16][16];  // inputs of the 4 x 4 leaves around the quad, rounded to T once
                                             // (complex128: split into float pairs, like sn)
     __shared__ C part[2][kLeafPerCta * 16];
-    if (done != nullptr && blockIdx.x == 0 && threadIdx.x <= kMaxPass) done[threadIdx.x * kDoneStride] = 0;
     auto rnd = [](double2 d) {
         C c;
         c.x = (T)d.x;
@@ -1787,10 +1822,47 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
     const int i = li & 15;
     T ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
     // The first group stages the near-field blocks and inputs in shared memory
-    // (and loads the epilogue's v, q) while the other two apply the far field,
-    // which needs no shared memory: the composed L2L and L2P (second), L2P (third).
+    // (and loads the epilogue's v, q); then every group applies one row of
+    // near offsets.  Only then does the kernel wait for the launch before it
+    // (the fused far field, whose CTAs let this grid start as they retire) and
+    // apply the far field: the composed L2L and L2P (second group), L2P (third).
     double2 vv = make_double2(0, 0);
     double qq = 0;
+    // bulk copies: thread 0 the near blocks, thread 1 + l the far-field blocks
+    // of leaf l (static operators, staged when fcc or fcl > 0)
+    __shared__ __align__(8) unsigned long long s_bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1 + kLeafPerCta);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_expect_copy(sn, near, 9 * 256 * (unsigned)sizeof(C), &s_bar);
+        mbar_arrive1(&s_bar);
+    } else if (threadIdx.x <= kLeafPerCta) {
+        const int l = threadIdx.x - 1, lf = q0 + l;
+        if (staged) {
+            int ne = 0, coff = 0, nl = 0;
+            if (lf < nleaf && c_rowptr != nullptr)
+                for (int e = c_rowptr[lf]; e < c_rowptr[lf + 1]; e++, ne++) {
+                    const int ri = c_rin[e];
+                    if (ri > 0) bulk_expect_copy(sUc + (size_t)(l * fcc + coff) * 16, cm + c_moff[e], 16 * ri * (unsigned)sizeof(C), &s_bar);
+                    s_ecol[l][ne] = c_col[e];
+                    s_erin[l][ne] = ri;
+                    s_ecoff[l][ne] = coff;
+                    coff += ri;
+                }
+            if (lf < nleaf && l2p_rowptr != nullptr && l2p_rowptr[lf + 1] > l2p_rowptr[lf]) {
+                const int e = l2p_rowptr[lf];
+                nl = l2p_rin[e];
+                if (nl > 0) bulk_expect_copy(sUl + (size_t)l * fcl * 16, l2p + l2p_moff[e], 16 * nl * (unsigned)sizeof(C), &s_bar);
+            }
+            s_nce[l] = ne;
+            s_ncc[l] = coff;
+            s_nl[l] = nl;
+        }
+        mbar_arrive1(&s_bar);
+    }
     if (grp == 0) {
         const int t0 = li;  // 0 .. 16 kLeafPerCta - 1
         constexpr int kThr = 16 * kLeafPerCta;
@@ -1816,25 +1888,132 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
             }
             vq[pos][j] = val;
         }
-        // 16-byte loads, several in flight per thread
-        constexpr int kVec = 9 * 256 * (int)sizeof(C) / 16;
-        constexpr int kIn = sizeof(C) == 16 ? 4 : 8;
-        const uint4* src = (const uint4*)near;
-        uint4* dst = (uint4*)sn;
-        for (int k0 = 0; k0 < kVec; k0 += kIn * kThr) {
-            uint4 tmp[kIn];
-#pragma unroll
-            for (int u = 0; u < kIn; u++) {
-                const int k = k0 + t0 + u * kThr;
-                if (k < kVec) tmp[u] = src[k];
+    } else if (!staged && leaf < nleaf) {
+        // meanwhile the far-field groups bring their operator blocks (static)
+        // into L2, so that after the wait only the locals come from afar
+        const bool composed = grp == 1;
+        const int* rowptr = composed ? c_rowptr : l2p_rowptr;
+        if (rowptr != nullptr)
+            for (int e = rowptr[leaf]; e < rowptr[leaf + 1]; e++) {
+                const C* U = composed ? cm + c_moff[e] : l2p + l2p_moff[e];
+                const int ri = composed ? c_rin[e] : l2p_rin[e];
+                for (int off = i * 128; off < 16 * ri * (int)sizeof(C); off += 16 * 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)U + off));
             }
+    }
+    // the copies have landed (a wait that gives up flags the error and waits once more)
+    if (!mbar_wait(&s_bar, 0)) {
+        atomicExch(err, 1);
+        mbar_wait(&s_bar, 0);
+    }
+    __syncthreads();
+    if (leaf < nleaf) {
+        const int l = leaf - q0;
+        // complex128: the near blocks and inputs are float pairs, multiplied in double-float
+        float dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f}, eh[2] = {0.f, 0.f}, el[2] = {0.f, 0.f};
 #pragma unroll
-            for (int u = 0; u < kIn; u++) {
-                const int k = k0 + t0 + u * kThr;
-                if (k < kVec) dst[k] = tmp[u];
+        for (int sx = 0; sx < 3; sx++) {
+            const int o = grp * 3 + sx;  // offset (sx - 1, grp - 1); outside the domain vq holds zeros
+            const C* vs = vq[(1 + (l >> 1) + grp - 1) * 4 + 1 + (l & 1) + sx - 1];
+            const C* B = sn + o * 256 + i;
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                if constexpr (sizeof(T) == 8) {
+                    df_cmac(dh[0], dl[0], eh[0], el[0], as_df(B[j * 16]), as_df(vs[j]));
+                    df_cmac(dh[1], dl[1], eh[1], el[1], as_df(B[(j + 1) * 16]), as_df(vs[j + 1]));
+                } else {
+                    cmac<T>(ar0, ai0, B[j * 16], vs[j]);
+                    cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
+                }
             }
         }
-    } else if (leaf < nleaf) {
+        if constexpr (sizeof(T) == 8) {
+            ar1 += ((double)dh[0] + (double)dl[0]) + ((double)dh[1] + (double)dl[1]);
+            ai1 += ((double)eh[0] + (double)el[0]) + ((double)eh[1] + (double)el[1]);
+        }
+    }
+    // the far field reads what the launch before wrote (a no-op without a programmatic dependency)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (done != nullptr && blockIdx.x == 0 && threadIdx.x <= kMaxPass) done[threadIdx.x * kDoneStride] = 0;
+    if (staged) {
+        // the locals of the staged columns (every load in flight at once), then
+        // the products from shared memory
+        constexpr int kPer = kLeafStageCols / 16;
+        const int l = leaf - q0;
+        if (grp != 0 && leaf < nleaf) {
+            const bool composed = grp == 1;
+            const int nc = composed ? s_ncc[l] : s_nl[l];
+            C w[kPer], w2[kPer];
+            bool two[kPer];
+#pragma unroll
+            for (int m = 0; m < kPer; m++) {
+                const int c = i + 16 * m;
+                two[m] = false;
+                if (c < nc) {
+                    const C *a = nullptr, *a2 = nullptr;
+                    if (composed) {
+                        int k = 0;
+                        while (k + 1 < s_nce[l] && s_ecoff[l][k + 1] <= c) k++;
+                        const size_t o = (size_t)s_ecol[l][k] * ldc + (c - s_ecoff[l][k]);
+                        a = lcA + o;
+                        a2 = lcB ? lcB + o : nullptr;
+                    } else {
+                        a = lc + (size_t)leaf * ldl + c;
+                        a2 = lc2 ? lc2 + (size_t)leaf * ldl + c : nullptr;
+                    }
+                    w[m] = *a;
+                    if (a2) {
+                        w2[m] = *a2;
+                        two[m] = true;
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < kPer; m++) {
+                const int c = i + 16 * m;
+                if (c < nc) {
+                    C x = w[m];
+                    if (two[m]) {
+                        if constexpr (sizeof(T) == 8) {
+                            x = df_bits(df4_add(as_df(x), as_df(w2[m])));
+                        } else {
+                            x.x += w2[m].x;
+                            x.y += w2[m].y;
+                        }
+                    }
+                    (composed ? suc + l * fcc : sul + l * fcl)[c] = x;
+                }
+            }
+        }
+        __syncthreads();
+        if (grp != 0 && leaf < nleaf) {
+            const bool composed = grp == 1;
+            const int nc = composed ? s_ncc[l] : s_nl[l];
+            const C* U = composed ? sUc + (size_t)l * fcc * 16 + i : sUl + (size_t)l * fcl * 16 + i;
+            const C* u = composed ? suc + l * fcc : sul + l * fcl;
+            float dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f}, eh[2] = {0.f, 0.f}, el[2] = {0.f, 0.f};
+            int c = 0;
+            for (; c + 1 < nc; c += 2) {
+                if constexpr (sizeof(T) == 8) {
+                    df_cmac(dh[0], dl[0], eh[0], el[0], as_df(U[c * 16]), as_df(u[c]));
+                    df_cmac(dh[1], dl[1], eh[1], el[1], as_df(U[(c + 1) * 16]), as_df(u[c + 1]));
+                } else {
+                    cmac<T>(ar0, ai0, U[c * 16], u[c]);
+                    cmac<T>(ar1, ai1, U[(c + 1) * 16], u[c + 1]);
+                }
+            }
+            if (c < nc) {
+                if constexpr (sizeof(T) == 8)
+                    df_cmac(dh[0], dl[0], eh[0], el[0], as_df(U[c * 16]), as_df(u[c]));
+                else
+                    cmac<T>(ar0, ai0, U[c * 16], u[c]);
+            }
+            if constexpr (sizeof(T) == 8) {
+                ar0 += ((double)dh[0] + (double)dl[0]) + ((double)dh[1] + (double)dl[1]);
+                ai0 += ((double)eh[0] + (double)el[0]) + ((double)eh[1] + (double)el[1]);
+            }
+        }
+    } else if (grp != 0 && leaf < nleaf) {
         const bool composed = grp == 1;
         const int* rowptr = composed ? c_rowptr : l2p_rowptr;
         if (rowptr != nullptr) {
@@ -1881,32 +2060,6 @@ __global__ void __launch_bounds__(48 * kLeafPerCta) leaf_apply_kernel(int nleaf,
                 ar0 += ((double)dh[0] + (double)dl[0]) + ((double)dh[1] + (double)dl[1]);
                 ai0 += ((double)eh[0] + (double)el[0]) + ((double)eh[1] + (double)el[1]);
             }
-        }
-    }
-    __syncthreads();
-    if (leaf < nleaf) {
-        const int l = leaf - q0;
-        // complex128: the near blocks and inputs are float pairs, multiplied in double-float
-        float dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f}, eh[2] = {0.f, 0.f}, el[2] = {0.f, 0.f};
-#pragma unroll
-        for (int sx = 0; sx < 3; sx++) {
-            const int o = grp * 3 + sx;  // offset (sx - 1, grp - 1); outside the domain vq holds zeros
-            const C* vs = vq[(1 + (l >> 1) + grp - 1) * 4 + 1 + (l & 1) + sx - 1];
-            const C* B = sn + o * 256 + i;
-#pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-                if constexpr (sizeof(T) == 8) {
-                    df_cmac(dh[0], dl[0], eh[0], el[0], as_df(B[j * 16]), as_df(vs[j]));
-                    df_cmac(dh[1], dl[1], eh[1], el[1], as_df(B[(j + 1) * 16]), as_df(vs[j + 1]));
-                } else {
-                    cmac<T>(ar0, ai0, B[j * 16], vs[j]);
-                    cmac<T>(ar1, ai1, B[(j + 1) * 16], vs[j + 1]);
-                }
-            }
-        }
-        if constexpr (sizeof(T) == 8) {
-            ar1 += ((double)dh[0] + (double)dl[0]) + ((double)dh[1] + (double)dl[1]);
-            ai1 += ((double)eh[0] + (double)el[0]) + ((double)eh[1] + (double)el[1]);
         }
     }
     C mine;
@@ -2634,13 +2787,28 @@ void run_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const double* 
     const BsrDev* l2p = far ? &d.lv[L].down : nullptr;
     const bool comp = far && L - 1 >= t.top;
     const C* cm = comp ? (const C*)(sizeof(T) == 8 ? d.leafc.mdf : d.leafc.m32) : nullptr;
-    leaf_apply_kernel<T><<<(unsigned)((nleaf + kLeafPerCta - 1) / kLeafPerCta), 48 * kLeafPerCta, 0, s>>>(
-        nleaf, d.nbr, nearp, l2p ? l2p->rowptr : nullptr, l2p ? l2p->moff : nullptr, l2p ? l2p->rin : nullptr,
-        l2p ? (const C*)(sizeof(T) == 8 ? l2p->mdf : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0, far ? b.lc[L] : nullptr, nullptr,
-        comp ? d.leafc.rowptr : nullptr, comp ? d.leafc.col : nullptr, comp ? d.leafc.moff : nullptr, comp ? d.leafc.rin : nullptr, cm,
-        comp ? d.lv[L - 1].Ri : 0, comp ? b.lc[L - 1] : nullptr, comp && L - 1 > t.top ? b.lcd[L - 1] : nullptr, (const double2*)v, d.potential ? nullptr : d.q,
-        t.prm.kappa * t.prm.kappa, (double2*)out, far ? d.fz.done : nullptr);
-    CK(cudaGetLastError());
+    // programmatic serialization: the leaf CTAs start (near field) while the
+    // far field's CTAs retire, and wait in the kernel for its writes
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)((nleaf + kLeafPerCta - 1) / kLeafPerCta));
+    cfg.blockDim = dim3(48 * kLeafPerCta);
+    cfg.dynamicSmemBytes = (size_t)kLeafPerCta * 17 * (d.fz.leaf_fcc + d.fz.leaf_fcl) * sizeof(C);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = far ? 1 : 0;
+    CK(cudaLaunchKernelEx(&cfg, leaf_apply_kernel<T>, nleaf, (const int*)d.nbr, nearp, l2p ? (const int*)l2p->rowptr : nullptr,
+                          l2p ? (const long*)l2p->moff : nullptr, l2p ? (const int*)l2p->rin : nullptr,
+                          l2p ? (const C*)(sizeof(T) == 8 ? l2p->mdf : l2p->m32) : nullptr, far ? d.lv[L].Ri : 0,
+                          far ? (const C*)b.lc[L] : nullptr, (const C*)nullptr, comp ? (const int*)d.leafc.rowptr : nullptr,
+                          comp ? (const int*)d.leafc.col : nullptr, comp ? (const long*)d.leafc.moff : nullptr,
+                          comp ? (const int*)d.leafc.rin : nullptr, cm, comp ? d.lv[L - 1].Ri : 0, comp ? (const C*)b.lc[L - 1] : nullptr,
+                          comp && L - 1 > t.top ? (const C*)b.lcd[L - 1] : nullptr, (const double2*)v, (const double*)(d.potential ? nullptr : d.q),
+                          (double)(t.prm.kappa * t.prm.kappa), (double2*)out, far ? d.fz.done : (int*)nullptr, d.fz.leaf_fcc,
+                          d.fz.leaf_fcl, d.err));
     mark(prof, 4, s);
 }
 
@@ -2813,6 +2981,10 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
         build_group(d.m2l, m2l_passes, m2l_hosts, m2l_ldx, 0);
         CK(cudaFuncSetAttribute(stream_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, StreamCfg<float>::kCta));
         CK(cudaFuncSetAttribute(stream_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, StreamCfg<double>::kCta));
+        CK(cudaFuncSetAttribute(leaf_apply_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kLeafPerCta * 17 * 2 * kLeafStageCols * (int)sizeof(float2)));
+        CK(cudaFuncSetAttribute(leaf_apply_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kLeafPerCta * 17 * 2 * kLeafStageCols * (int)sizeof(double2)));
         d.fz.ctas[0] = fused_ctas<double>();
         d.fz.ctas[1] = fused_ctas<float>();
         // single right-hand side: the first up pass above the leaves reads the leaf
@@ -2831,6 +3003,32 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
             for (size_t e = 0; e < leafc.rin.size(); e++) d.fz.leaf_cmacs += 16.0 * leafc.rin[e];
             upload_bsr(upc, d.lv[L - 1].upc);
             upload_bsr(leafc, d.leafc);
+        }
+        // the leaf kernel stages its far-field blocks in shared memory when
+        // every leaf has at most kLeafEnt composed blocks, one L2P block and
+        // kLeafStageCols columns of each
+        {
+            const BsrHost& U = h.lv[L].down;
+            int fcc = 0, fcl = 0;
+            bool ok = t.top <= L;
+            for (int b = 0; ok && b < U.nrows; b++) {
+                const int ne = U.rowptr[b + 1] - U.rowptr[b];
+                if (ne > 1) ok = false;
+                if (ne == 1) fcl = std::max(fcl, U.rin[U.rowptr[b]]);
+            }
+            if (compose)
+                for (int b = 0; ok && b < leafc.nrows; b++) {
+                    int cols = 0;
+                    for (int e = leafc.rowptr[b]; e < leafc.rowptr[b + 1]; e++) cols += leafc.rin[e];
+                    if (leafc.rowptr[b + 1] - leafc.rowptr[b] > kLeafEnt) ok = false;
+                    fcc = std::max(fcc, cols);
+                }
+            for (size_t e = 0; ok && e < U.moff.size(); e++) ok = U.moff[e] % 2 == 0;  // 16-byte aligned blocks
+            if (compose)
+                for (size_t e = 0; ok && e < leafc.moff.size(); e++) ok = leafc.moff[e] % 2 == 0;
+            ok = ok && fcc <= kLeafStageCols && fcl <= kLeafStageCols && fcc + fcl > 0;
+            d.fz.leaf_fcc = ok ? fcc : 0;
+            d.fz.leaf_fcl = ok ? fcl : 0;
         }
         for (int nu = t.top; nu <= L; nu++) {
             // single-right-hand-side coefficients, zero once: rows no pass writes read as zero

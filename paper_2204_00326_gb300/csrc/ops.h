@@ -83,6 +83,7 @@ struct Fused {
     int* done = nullptr;           // per pass: rows written in the running application; then the piece counter
     double cmacs = 0;              // complex multiply-adds of one launch (realised ranks)
     double leaf_cmacs = 0;         // ... of the leaf kernel after it (near field, L2P, composed L2L)
+    int leaf_fcc = 0, leaf_fcl = 0;  // leaf kernel: composed and L2P columns staged a leaf (0, 0: not staged)
 };
 
 // One captured application (per precision), replayed while the vector

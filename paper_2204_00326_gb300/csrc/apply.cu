@@ -85,6 +85,11 @@ struct Sched {
     int target[kMaxPass];       // per pass: rows it writes
     int dphase[kMaxPass];       // per pass: latest phase among the passes it reads (-1: none)
     unsigned pub;               // passes read by another pass of the launch: the only ones counted
+    // static tables the launch reads (chunk records, column maps), prefetched
+    // into L2 at the start: the operators stream past them evict_first
+    const char* pf_ptr[kMaxPass + 1];
+    int pf_bytes[kMaxPass + 1];
+    int npf;
 };
 
 template <typename T>
@@ -127,6 +132,15 @@ __device__ __forceinline__ void tma_load(void* dst, const void* src, unsigned by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// The same with an L2 cache policy (evict_first for data read once).
+__device__ __forceinline__ void tma_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar, unsigned long long pol)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
                  : "memory");
 }
 
@@ -799,6 +813,14 @@ __global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4
     C* xs = (C*)(wb + 2 * Cfg::kStage);
     unsigned long long* bar = (unsigned long long*)(wb + 2 * Cfg::kStage + Cfg::kXs);
     const int wg = warp * gridDim.x + blockIdx.x;  // the CTAs' first warps first
+    {
+        const int gt = wg * 32 + lane, nt = gridDim.x * kStreamWarps * 32;
+        for (int r = 0; r < sc.npf; r++)
+            for (long off = (long)gt * 128; off < sc.pf_bytes[r]; off += (long)nt * 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(sc.pf_ptr[r] + off));
+    }
+    unsigned long long pol;  // the operators are read once an application
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
 
     // ---- scheduler (warp-uniform, except the lane-0 prefetches) ----
     Slice cs;
@@ -874,10 +896,10 @@ __global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         unsigned bytes;
         const char* src = chunk_src<T>(g, recs[2 * cur.c], recs[2 * cur.c + 1], bytes);
-        tma_load(stage(0), src, bytes, &bar[0]);
+        tma_load(stage(0), src, bytes, &bar[0], pol);
         if (n1.c >= 0) {
             src = chunk_src<T>(g, recs[2 * n1.c], recs[2 * n1.c + 1], bytes);
-            tma_load(stage(1), src, bytes, &bar[1]);
+            tma_load(stage(1), src, bytes, &bar[1], pol);
         }
     }
     __syncwarp();
@@ -976,7 +998,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             unsigned nbytes;
             const char* src = chunk_src<T>(g, fa, fb, nbytes);
-            tma_load(stage(s), src, nbytes, &bar[s]);
+            tma_load(stage(s), src, nbytes, &bar[s], pol);
         }
         if (!have_x) {
 #pragma unroll
@@ -2237,6 +2259,7 @@ void upload_tables(Group& g, const PassCut& pc)
     g.rbase.push_back(drb);
     g.cbase.push_back(dcb);
     g.xmap.push_back(dxm);
+    g.xmap_n.push_back((int)pc.xmap.size());
 }
 
 void finish_group(Group& g, const std::vector<int4>& recs, int pld)
@@ -2711,6 +2734,13 @@ void launch_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const doubl
     for (int ph = 0; ph < FP.nph; ph++) sc.phdeps[ph] = FP.phdeps[ph];
     sc.npieces = FP.npieces;
     sc.chain_first = FP.chain_first ? 1 : 0;
+    sc.npf = 0;
+    sc.pf_ptr[sc.npf] = (const char*)FP.chunks;
+    sc.pf_bytes[sc.npf++] = FP.nch * (int)(2 * sizeof(int4));
+    for (size_t p = 0; p < F.g.passes.size() && sc.npf <= kMaxPass; p++) {
+        sc.pf_ptr[sc.npf] = (const char*)F.g.xmap[p];
+        sc.pf_bytes[sc.npf++] = F.g.xmap_n[p] * (int)sizeof(int);
+    }
     sc.pieces = FP.pieces;
     sc.next_piece = F.done + kMaxPass * kDoneStride;
     for (size_t p = 0; p < F.g.passes.size(); p++) {

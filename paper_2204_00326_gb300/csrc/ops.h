@@ -49,6 +49,7 @@ struct Group {
     std::vector<long*> rbase;
     std::vector<int*> cbase;
     std::vector<int*> xmap;
+    std::vector<int> xmap_n;  // per pass: columns in xmap
 };
 
 // Every tree pass of a single-right-hand-side application in one cooperative

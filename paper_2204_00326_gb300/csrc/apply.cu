@@ -76,7 +76,7 @@ struct Sched {
     unsigned phdeps[kMaxPhase]; // passes read by the passes of each phase
     int wlo[kMaxPhase];         // the warps sharing each phase: wlo .. wlo + wn - 1, in the
     int wn[kMaxPhase];          // order (warp of its CTA, CTA)
-    int chain_first;            // a warp takes pieces only when its chain shares are done
+    int chain_split;            // the chain has warps of its own: they take no pieces
     // bulk list: the passes with slack, cut into pieces handed out in order
     int npieces;
     const int4* pieces;         // per piece: {first chunk, end chunk, partial slot, pass}
@@ -830,7 +830,12 @@ __global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4
     int4 pq = make_int4(0, 0, 0, -1);     // lane 0: the next piece (pass -1: none left)
     int nid = 0;                          // lane 0: id of the piece after it
     unsigned ready = 0, seen = 0;         // passes known complete (acquired / polled)
-    if (lane == 0 && sc.npieces > 0) {
+    // A chain warp of its own (a share after phase 0) reserves no piece: a
+    // reserved piece waits for its warp, and a chain warp may wait for the
+    // pass that piece belongs to (an L2L reads the M2L of its level).
+    Slice later;
+    const bool takes_pieces = !(sc.chain_split && slice_from(sc, 1, wg, later));
+    if (lane == 0 && sc.npieces > 0 && takes_pieces) {
         const int id0 = atomicAdd(sc.next_piece, 1);
         nid = atomicAdd(sc.next_piece, 1);
         if (id0 < sc.npieces) pq = sc.pieces[id0];
@@ -848,7 +853,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4
             bool chain;
             if (!hc)
                 chain = false;
-            else if (!hb || sc.chain_first)
+            else if (!hb)
                 chain = true;
             else if ((sc.phdeps[cs.k] & ~(ready | seen)) == 0)
                 chain = true;
@@ -2535,7 +2540,7 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
                     for (int r = 0; r < hs[p]->nrows; r++) after0[1] += chunks(p, r);
         P.wlo.clear();
         P.wn.clear();
-        P.chain_first = split && dynamic;
+        P.chain_split = split && dynamic;
         if (split) {
             const int W = F.ctas[k] * kStreamWarps;
             int wc = W;  // chain warps
@@ -2733,7 +2738,7 @@ void launch_fused(const Tree& t, const OpsDev& d, const FBufs<T>& b, const doubl
     fused_shares(FP, warps, sc.kpw, sc.sbase);
     for (int ph = 0; ph < FP.nph; ph++) sc.phdeps[ph] = FP.phdeps[ph];
     sc.npieces = FP.npieces;
-    sc.chain_first = FP.chain_first ? 1 : 0;
+    sc.chain_split = FP.chain_split ? 1 : 0;
     sc.npf = 0;
     sc.pf_ptr[sc.npf] = (const char*)FP.chunks;
     sc.pf_bytes[sc.npf++] = FP.nch * (int)(2 * sizeof(int4));

@@ -68,7 +68,7 @@ struct FusedPlan {
     std::vector<int> base;         // per chain phase: first chunk; base[nph] = chain chunks
     std::vector<unsigned> phdeps;  // per chain phase: passes read by its passes
     std::vector<int> wlo, wn;      // per chain phase: the warps sharing it (empty: every warp)
-    bool chain_first = false;      // pieces only after a warp's chain shares
+    bool chain_split = false;      // the chain phases after the first have warps of their own (which take no pieces)
     int npieces = 0;               // bulk pieces (chunk ranges of one row), taken in order
     int4* pieces = nullptr;        // per piece: {first chunk, end chunk, partial slot, pass}
     size_t part = 0;               // complex elements of chunk partials it uses

@@ -139,3 +139,31 @@ def test_nbody_argument_errors(N):
         op.close()
     with pytest.raises(N.DafmmError):
         N.build_tree(N.make_params(50.0, kernel=2), 64)
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9, 1e-12])
+def test_repeated_applications_complete_without_a_stall(N, eps):
+    """N = 65536 points at three eps_nca, five applications a precision.
+    In this tree an L2L reads the M2L of its level, a pass with slack that
+    the fused launch hands out as pieces; every application must finish
+    without a wait giving up (op.sync() reports one) and in milliseconds
+    (a wait that gives up takes 0.2 s), with the error eps_nca allows."""
+    w = W.NBODY256_K50
+    op = _op(N, w.n_side, w.kappa, eps=eps)
+    try:
+        fd = torch.as_tensor(W.random_vector(w.N, 1, seed=65)[:, 0], device="cuda")
+        direct = torch.empty_like(fd)
+        N.dafmm_nbody_direct(op.tree, fd, direct)
+        op.sync()
+        for prec, tol in ((N.DAFMM_FP64, 1e3 * eps), (N.DAFMM_MIXED, max(1e3 * eps, 2e-5))):
+            u = torch.empty_like(fd)
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                op.potential(fd, u, precision=prec)
+                e1.record()
+                op.sync()
+                assert e0.elapsed_time(e1) < 50.0, (eps, prec, e0.elapsed_time(e1))
+                assert (torch.linalg.norm(u - direct) / torch.linalg.norm(direct)).item() < tol
+    finally:
+        op.close()

@@ -714,7 +714,7 @@ constexpr int kPiece = 4;  // chunks per bulk piece
 // Warps given to the chain phases after the first: this many times the
 // chain's share of the chunks after the first phase (the rest stream the
 // slack passes); the chain's dependent steps need the margin.
-constexpr double kChainShare64 = 1.25, kChainShare128 = 1.0;
+constexpr double kChainShare64 = 1.4, kChainShare128 = 1.0;
 // Plans: the slack passes as pieces taken in order (else in phases of their
 // own), and the chain phases after the first on their own warps.
 constexpr bool kPieces128 = true, kSplit128 = true;

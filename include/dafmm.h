@@ -434,6 +434,20 @@ int dafmm_set_contrast(dafmm_ops* ops, const double* q_dev, void* stream);
 int dafmm_debug_stall(dafmm_ops* ops, int pass);
 
 /*
+ * dafmm_debug_leaf_staging -- test support (no counterpart in the paper).
+ * The leaf kernel of a single-right-hand-side application copies its
+ * far-field blocks (the L2L from level L-1 composed with L2P, and L2P:
+ * Section 4's downward pass) into shared memory before it waits for the far
+ * field, when every leaf has at most 8 composed blocks, one L2P block and
+ * 64 columns of each; else it reads them from global memory.  enable = 0
+ * forces the global-memory path, 1 restores the planned one (both give the
+ * same result bit for bit: the same products in the same order).  Drops the
+ * handle's captured graphs.  Errors: DAFMM_EBADARG for a NULL handle or
+ * enable outside 0 .. 1.
+ */
+int dafmm_debug_leaf_staging(dafmm_ops* ops, int enable);
+
+/*
  * dafmm_set_batched_kernel -- which kernel runs the tree passes (P2M, M2M,
  * M2L, L2L) of a complex64 (DAFMM_MIXED) application with several
  * right-hand sides: 0 automatic (currently the CUDA cores: faster at the

@@ -3062,8 +3062,8 @@ void upload_ops(const Tree& t, OpsHost& h, OpsDev& d)
             if (compose)
                 for (size_t e = 0; ok && e < leafc.moff.size(); e++) ok = leafc.moff[e] % 2 == 0;
             ok = ok && fcc <= kLeafStageCols && fcl <= kLeafStageCols && fcc + fcl > 0;
-            d.fz.leaf_fcc = ok ? fcc : 0;
-            d.fz.leaf_fcl = ok ? fcl : 0;
+            d.fz.leaf_fcc = d.fz.leaf_fcc_plan = ok ? fcc : 0;
+            d.fz.leaf_fcl = d.fz.leaf_fcl_plan = ok ? fcl : 0;
         }
         for (int nu = t.top; nu <= L; nu++) {
             // single-right-hand-side coefficients, zero once: rows no pass writes read as zero
@@ -3165,6 +3165,21 @@ void set_batched_kernel(OpsDev& d, int mode)
     if (mode == d.batched_kernel) return;
     d.batched_kernel = mode;
     // captured applications hold the previous kernels
+    for (auto& row : d.gc)
+        for (auto& G : row) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.graph) cudaGraphDestroy(G.graph);
+            G = GraphCache();
+        }
+}
+
+void set_leaf_staging(OpsDev& d, bool on)
+{
+    const int fcc = on ? d.fz.leaf_fcc_plan : 0, fcl = on ? d.fz.leaf_fcl_plan : 0;
+    if (fcc == d.fz.leaf_fcc && fcl == d.fz.leaf_fcl) return;
+    d.fz.leaf_fcc = fcc;
+    d.fz.leaf_fcl = fcl;
+    // captured applications hold the previous launch of the leaf kernel
     for (auto& row : d.gc)
         for (auto& G : row) {
             if (G.exec) cudaGraphExecDestroy(G.exec);

@@ -514,6 +514,15 @@ int dafmm_debug_stall(dafmm_ops* ops, int pass)
     });
 }
 
+int dafmm_debug_leaf_staging(dafmm_ops* ops, int enable)
+{
+    return guarded([&] {
+        if (!ops) fail(DAFMM_EBADARG, "NULL argument");
+        if (enable != 0 && enable != 1) fail(DAFMM_EBADARG, "enable must be 0 or 1");
+        set_leaf_staging(ops->dev, enable == 1);
+    });
+}
+
 int dafmm_stats(const dafmm_ops* ops, dafmm_stats_t* stats)
 {
     return guarded([&] {

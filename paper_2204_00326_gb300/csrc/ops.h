@@ -85,6 +85,7 @@ struct Fused {
     double cmacs = 0;              // complex multiply-adds of one launch (realised ranks)
     double leaf_cmacs = 0;         // ... of the leaf kernel after it (near field, L2P, composed L2L)
     int leaf_fcc = 0, leaf_fcl = 0;  // leaf kernel: composed and L2P columns staged a leaf (0, 0: not staged)
+    int leaf_fcc_plan = 0, leaf_fcl_plan = 0;  // ... as planned (the staging can be switched off)
 };
 
 // One captured application (per precision), replayed while the vector
@@ -149,6 +150,7 @@ void free_ops(OpsDev& d);
 void profile_enable(OpsDev& d, bool on);
 void set_batched_kernel(OpsDev& d, int mode);
 void set_batched_grid(OpsDev& d, int ctas_per_sm);
+void set_leaf_staging(OpsDev& d, bool on);
 void profile_read(OpsDev& d, dafmm_profile_t& p);
 // Make sure scratch holds nrhs right-hand sides.
 void ensure_scratch(const Tree& t, OpsDev& d, int nrhs);

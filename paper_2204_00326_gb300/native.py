@@ -185,6 +185,7 @@ _sig = {
     "dafmm_batch_destroy": ([_P], ctypes.c_int),
     "dafmm_sync": ([_P, _P], ctypes.c_int),
     "dafmm_debug_stall": ([_P, ctypes.c_int], ctypes.c_int),
+    "dafmm_debug_leaf_staging": ([_P, ctypes.c_int], ctypes.c_int),
     "dafmm_potential": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "dafmm_set_contrast": ([_P, _P, _P], ctypes.c_int),
     "gmres_solve": ([_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(gmres_opts), ctypes.POINTER(gmres_stats), _P], ctypes.c_int),
@@ -425,6 +426,12 @@ def dafmm_debug_stall(ops: int, pass_index: int) -> None:
     pass `pass_index` that is never written (bounded), so dafmm_sync reports
     DAFMM_ETIMEOUT.  -1 cancels."""
     _check(lib.dafmm_debug_stall(ops, int(pass_index)))
+
+
+def dafmm_debug_leaf_staging(ops: int, enable: bool) -> None:
+    """Test support: the leaf kernel's far-field blocks staged in shared
+    memory (True, the planned path) or read from global memory (False)."""
+    _check(lib.dafmm_debug_leaf_staging(ops, 1 if enable else 0))
 
 
 def dafmm_stats(ops: int) -> dafmm_stats_t:

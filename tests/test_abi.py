@@ -99,6 +99,7 @@ def test_null_and_device_errors_are_status_codes():
     assert lib.hodlr_solve(None, 1, None, None, 0, None) == N.DAFMM_EBADARG
     assert lib.gmres_solve(None, None, 1, None, None, None, None, None) == N.DAFMM_EBADARG
     assert lib.dafmm_set_batched_kernel(None, 0) == N.DAFMM_EBADARG
+    assert lib.dafmm_debug_leaf_staging(None, 1) == N.DAFMM_EBADARG
     buf = ctypes.create_string_buffer(256)
     assert lib.dafmm_last_error(buf, 256) == N.DAFMM_EBADARG
     assert b"NULL" in buf.value

@@ -274,3 +274,25 @@ def test_stalled_pass_times_out_and_handle_recovers(N, op128):
     again = op128.matvec(v, precision=N.DAFMM_MIXED)
     op128.sync()
     assert torch.equal(again, ref)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_leaf_staging_and_global_path_agree(N, op128, precision):
+    """The leaf kernel's far-field blocks staged in shared memory (the planned
+    path) or read from global memory (the fallback for larger operators):
+    the same products in the same order, so the same result bit for bit, and
+    the oracle's rows at the usual bars."""
+    prec = N.DAFMM_MIXED if precision == "mixed" else N.DAFMM_FP64
+    v = torch.as_tensor(W.random_vector(op128.N, 1, seed=78)[:, 0], device="cuda")
+    staged = op128.matvec(v, precision=prec)
+    N.dafmm_debug_leaf_staging(op128.ops, False)
+    try:
+        plain = op128.matvec(v, precision=prec)
+        again = op128.matvec(v, precision=prec)
+    finally:
+        N.dafmm_debug_leaf_staging(op128.ops, True)
+    op128.sync()
+    assert torch.equal(plain, staged) and torch.equal(again, staged)
+    assert torch.equal(op128.matvec(v, precision=prec), staged)
+    with pytest.raises(N.DafmmError):
+        N._check(N.lib.dafmm_debug_leaf_staging(op128.ops, 2))

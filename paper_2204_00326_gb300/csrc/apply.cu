@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <unordered_map>
 #include <mutex>
 #include <string>
 
@@ -719,6 +720,7 @@ constexpr double kChainShare64 = 1.4, kChainShare128 = 1.0;
 // own), and the chain phases after the first on their own warps.
 constexpr bool kPieces128 = true, kSplit128 = true;
 constexpr bool kPieces64 = false, kSplit64 = true;
+constexpr bool kDedupChunks = true;  // equal chunks of a pass share one copy of their matrix
 
 // One scheduled chunk: c (-1: none); kind 0: chain (aux = phase, end = the
 // share's end), 1: bulk (aux = the piece's partial slot, end = the piece's end).
@@ -2240,6 +2242,66 @@ PassCut cut_pass(const BsrHost& b, int pass, int ldx, int accumulate, const std:
 }
 
 // Append row r of a cut pass to the list, with its chunk range.
+// A chunk whose matrix equals an earlier chunk's of the same pass, entry for
+// entry as stored (complex64 when `c64`, else complex128), takes the earlier
+// chunk's address: the same products from the same numbers.  On a uniform
+// grid the entry table depends only on the offset between boxes, so boxes
+// with the same neighbourhood get the same blocks; the copies then come
+// from L2 instead of DRAM.
+void dedup_chunks(std::vector<int4>& recs, const std::vector<const BsrHost*>& hs, bool c64)
+{
+    std::vector<std::unordered_map<unsigned long long, std::vector<long>>> seen(hs.size());
+    auto entry = [&](const BsrHost& B, long elem, long k, unsigned (&w)[4]) {
+        const cd z = B.mats[elem + k];
+        if (c64) {
+            const float re = (float)z.real(), im = (float)z.imag();
+            std::memcpy(&w[0], &re, 4);
+            std::memcpy(&w[1], &im, 4);
+            w[2] = w[3] = 0;
+        } else {
+            const double re = z.real(), im = z.imag();
+            std::memcpy(&w[0], &re, 8);
+            std::memcpy(&w[2], &im, 8);
+        }
+    };
+    const long nch = (long)(recs.size() / 2);
+    for (long c = 0; c < nch; c++) {
+        const int4 a = recs[2 * c];
+        int4& b = recs[2 * c + 1];
+        const int p = a.x & 0xff;
+        const BsrHost& B = *hs[p];
+        const int ro = (a.x >> 16) & 0xffff;
+        const long n = (long)(ro + (ro & 1)) * a.z;
+        const long elem = (long)(unsigned)b.x | ((long)b.y << 32);
+        unsigned long long h = 1469598103934665603ull ^ ((unsigned long long)ro << 32 | (unsigned)a.z);
+        for (long k = 0; k < n; k++) {
+            unsigned w[4];
+            entry(B, elem, k, w);
+            for (unsigned x : w) h = (h ^ x) * 1099511628211ull;
+        }
+        long same = -1;
+        for (long e : seen[p][h]) {
+            bool eq = true;
+            for (long k = 0; k < n && eq; k++) {
+                unsigned w1[4], w2[4];
+                entry(B, elem, k, w1);
+                entry(B, e, k, w2);
+                eq = std::memcmp(w1, w2, sizeof(w1)) == 0;
+            }
+            if (eq) {
+                same = e;
+                break;
+            }
+        }
+        if (same < 0) {
+            seen[p][h].push_back(elem);
+        } else {
+            b.x = (int)(unsigned)(same & 0xffffffffL);
+            b.y = (int)(same >> 32);
+        }
+    }
+}
+
 void place_row(std::vector<int4>& out, const PassCut& pc, int r)
 {
     const int c0 = (int)(out.size() / 2);
@@ -2582,6 +2644,7 @@ void build_fused(const Tree& t, const OpsHost& h, OpsDev& d, const BsrHost* upc)
         P.npieces = (int)pieces.size();
         if (!pieces.empty()) upload_vec(pieces, &P.pieces);
         P.nch = (int)(recs.size() / 2);
+        if (kDedupChunks) dedup_chunks(recs, hs, k == 1);
         upload_vec(recs, &P.chunks);
         std::vector<int> zeros(std::max(P.nch, 1), 0);
         upload_vec(zeros, &P.cnt);

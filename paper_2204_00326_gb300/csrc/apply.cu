@@ -776,27 +776,29 @@ __device__ __forceinline__ bool bulk_finish(typename V2<T>::t* y, const typename
     return true;
 }
 
-// Every tree pass of one application.  Two lists of chunks: the chain (the
-// passes without slack, in phases, each warp with a static share of every
-// phase) and the bulk (the M2L levels with slack, cut into pieces of
-// kPiece chunks that warps take in order from a counter).  At the end of a
-// unit (a chain share or a piece) a warp takes the next chain share when the
-// passes it reads are complete, else the next piece when its inputs are
-// complete, else whichever reads the earlier phase; so bulk streams while the
-// chain waits on its short dependent steps.  The choice is made two chunks
+// Every tree pass of one application.  The chunk list is cut into phases,
+// each shared out in static, contiguous shares to a range of warps
+// (Sched::wlo, wn): phase 0 to every warp; with the chain split, the later
+// chain phases to the first warps and, in the static plan, each slack M2L
+// pass as a phase of its own to the others.  In the dynamic plan the slack
+// passes are instead pieces of kPiece chunks taken in order from a counter:
+// at the end of a unit (a share or a piece) a warp takes the next chain
+// share when the passes it reads are complete, else the next piece when its
+// inputs are complete, else whichever reads the earlier phase; with the
+// chain split, chain warps take no pieces.  The choice is made two chunks
 // ahead, so every chunk's matrix is copied in (TMA, two stages) before it is
 // needed.  Readiness is polled with relaxed loads issued an iteration early;
 // the first chunk of a pass waits (bounded) on its inputs' row counters with
-// acquire semantics.  Split chain rows are summed by the warp that holds
-// their first chunk, split bulk rows by their last piece, both in a fixed
-// order.  A warp counts its finished rows of a pass in its pass's counter
-// with one release when its run of chunks of that pass ends, and before it
-// waits on anything; a pass is complete only when every run of it is, so the
-// count arrives no later than it would row by row, and a waiting warp holds
-// no uncounted rows.  Passes that no other pass of the launch reads are not
-// counted.  Launched cooperatively, so every warp is resident; a warp blocks
-// only on rows of earlier phases, or on bulk inputs when it has no chain work
-// left, so the waits end.
+// acquire semantics.  Split rows of a phase are summed by the warp that
+// holds their first chunk, split rows of pieces by their last piece, both in
+// a fixed order.  A warp counts its finished rows of a pass in its pass's
+// counter with one release when its run of chunks of that pass ends, and
+// before it waits on anything; a pass is complete only when every run of it
+// is, so the count arrives no later than it would row by row, and a waiting
+// warp holds no uncounted rows.  Passes that no other pass of the launch
+// reads are not counted.  Launched cooperatively, so every warp is
+// resident; every phase reads only phases with a smaller index, warps take
+// their phases in index order and pieces in list order, so the waits end.
 template <typename T>
 __global__ void __launch_bounds__(32 * kStreamWarps, 3) stream_kernel(const int4* __restrict__ recs, const __grid_constant__ GroupArgs<T> g,
                                                                    const __grid_constant__ Sched sc, typename V2<T>::t* __restrict__ P,
